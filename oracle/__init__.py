@@ -1,0 +1,189 @@
+"""FP64 CPU oracle for checkerboard-overrelaxation gauge fixing (test infrastructure).
+
+A thin ctypes binding over ``culgt_oracle.c``: a plain, slow restatement of
+lattice Landau/Coulomb gauge fixing as defined in Vogt & Schröck, "cuLGT:
+Lattice Gauge Fixing on GPUs", Sec. 2. Only the tests, ``__graft_entry__.smoke``
+and the CPU-baseline leg of ``bench.py`` use this module; the CUDA library never
+does, and the two share no code.
+
+Link arrays are numpy ``complex128`` of shape ``(V, 4, Nc, Nc)`` in the canonical
+site order ``i = x1 + L1 (x2 + L2 (x3 + L3 x0))`` with dims ``L = (L0, L1, L2, L3)``,
+``L0`` = time.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "culgt_oracle.c")
+_LIB = os.path.join(_HERE, "libculgt_oracle.so")
+
+# -ffp-contract=off: no fused multiply-adds, so x86 and Arm builds round alike.
+CFLAGS = ["-O2", "-std=c11", "-fno-fast-math", "-ffp-contract=off", "-fPIC", "-shared", "-fopenmp"]
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (a second or two). Returns the library path."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    i, d = ctypes.c_int, ctypes.c_double
+    sig = {
+        "oracle_halfsweep": (None, [dp, ip, i, i, d, i]),
+        "oracle_sweep": (None, [dp, ip, i, d, i, i]),
+        "oracle_theta": (None, [dp, ip, i, dp, dp]),
+        "oracle_plaquette": (d, [dp, ip, i]),
+        "oracle_reunitarize": (None, [dp, ctypes.c_long, i]),
+        "oracle_unitarity_error": (d, [dp, ctypes.c_long, i]),
+        "oracle_landau_fix": (i, [dp, ip, i, d, i, d, i, i, i, ip, dp, dp]),
+        "oracle_theta_slice": (None, [dp, ip, i, i, dp, dp]),
+        "oracle_coulomb_fix": (i, [dp, ip, i, d, i, d, i, i, i, dp, ip, dp, dp]),
+        "oracle_local_gauge": (None, [dp, i, d, i, dp]),
+        "oracle_su2_local_max": (None, [dp, dp]),
+        "oracle_overrelax": (None, [dp, d, i, dp]),
+        "oracle_set_threads": (None, [i]),
+        "oracle_get_threads": (i, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dp(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    assert a.dtype in (np.float64, np.complex128)
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _dims(L):
+    arr = (ctypes.c_int * 4)(*[int(x) for x in L])
+    return arr
+
+
+def _check_links(U: np.ndarray, L, nc: int):
+    V = int(np.prod(L))
+    if U.shape != (V, 4, nc, nc) or U.dtype != np.complex128 or not U.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"links must be contiguous complex128 of shape {(V, 4, nc, nc)}")
+
+
+def set_threads(n: int) -> None:
+    _load().oracle_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(_load().oracle_get_threads())
+
+
+def halfsweep(U, L, nc, parity, omega, variant=0):
+    """Overrelaxation update of every site of one parity (0 = black = even), in place."""
+    _check_links(U, L, nc)
+    _load().oracle_halfsweep(_dp(U), _dims(L), nc, int(parity), float(omega), int(variant))
+
+
+def sweep(U, L, nc, omega, n_sweeps=1, variant=0):
+    """n_sweeps x (black half-sweep, white half-sweep), in place."""
+    _check_links(U, L, nc)
+    _load().oracle_sweep(_dp(U), _dims(L), nc, float(omega), int(variant), int(n_sweeps))
+
+
+def theta(U, L, nc):
+    """Returns (theta, F): theta = (1/V) sum_x tr[Delta Delta^+], F the Landau functional."""
+    _check_links(U, L, nc)
+    th, F = ctypes.c_double(), ctypes.c_double()
+    _load().oracle_theta(_dp(U), _dims(L), nc, ctypes.byref(th), ctypes.byref(F))
+    return th.value, F.value
+
+
+def plaquette(U, L, nc):
+    _check_links(U, L, nc)
+    return float(_load().oracle_plaquette(_dp(U), _dims(L), nc))
+
+
+def reunitarize(M, nc):
+    """In place over an array of Nc x Nc complex matrices (any leading shape)."""
+    assert M.dtype == np.complex128 and M.shape[-2:] == (nc, nc) and M.flags["C_CONTIGUOUS"]
+    _load().oracle_reunitarize(_dp(M), int(M.size // (nc * nc)), nc)
+
+
+def unitarity_error(M, nc):
+    M = np.ascontiguousarray(M, dtype=np.complex128)
+    return float(_load().oracle_unitarity_error(_dp(M), int(M.size // (nc * nc)), nc))
+
+
+def landau_fix(U, L, nc, omega, theta_target, max_sweeps, check_every=1, reunit_every=0, variant=0):
+    """Iterate sweeps until theta < theta_target or max_sweeps, in place.
+
+    Returns dict(converged, sweeps, theta, F)."""
+    _check_links(U, L, nc)
+    n, th, F = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    rc = _load().oracle_landau_fix(_dp(U), _dims(L), nc, float(omega), int(variant), float(theta_target),
+                                   int(max_sweeps), int(check_every), int(reunit_every), ctypes.byref(n),
+                                   ctypes.byref(th), ctypes.byref(F))
+    return {"converged": rc == 0, "sweeps": n.value, "theta": th.value, "F": F.value}
+
+
+def theta_slice(U, L, nc, t):
+    """(theta_t, F_t) of time slice t for the Coulomb functional (mu = 1..3)."""
+    _check_links(U, L, nc)
+    th, F = ctypes.c_double(), ctypes.c_double()
+    _load().oracle_theta_slice(_dp(U), _dims(L), nc, int(t), ctypes.byref(th), ctypes.byref(F))
+    return th.value, F.value
+
+
+def coulomb_fix(U, L, nc, omega, theta_target, max_sweeps, check_every=1, reunit_every=0, variant=0):
+    """Per-slice Coulomb gauge fixing, in place. Returns dict with per-slice arrays and the
+    accumulated gauge transformation g (V, Nc, Nc)."""
+    _check_links(U, L, nc)
+    V = int(np.prod(L))
+    g = np.zeros((V, nc, nc), dtype=np.complex128)
+    nt = int(L[0])
+    sw = (ctypes.c_int * nt)()
+    th = np.zeros(nt)
+    F = np.zeros(nt)
+    rc = _load().oracle_coulomb_fix(_dp(U), _dims(L), nc, float(omega), int(variant), float(theta_target),
+                                    int(max_sweeps), int(check_every), int(reunit_every), _dp(g), sw, _dp(th),
+                                    _dp(F))
+    return {"converged": rc == 0, "sweeps": np.array(list(sw)), "theta": th, "F": F, "g": g}
+
+
+def local_gauge(K, omega, variant=0):
+    """The overrelaxed local transformation g for one gathered K (Nc x Nc)."""
+    K = np.ascontiguousarray(K, dtype=np.complex128)
+    nc = K.shape[0]
+    g = np.zeros((nc, nc), dtype=np.complex128)
+    _load().oracle_local_gauge(_dp(K), nc, float(omega), int(variant), _dp(g))
+    return g
+
+
+def su2_local_max(w):
+    w = np.ascontiguousarray(w, dtype=np.complex128)
+    r = np.zeros((2, 2), dtype=np.complex128)
+    _load().oracle_su2_local_max(_dp(w), _dp(r))
+    return r
+
+
+def overrelax(g, omega, variant=0):
+    g = np.ascontiguousarray(g, dtype=np.complex128)
+    out = np.zeros((2, 2), dtype=np.complex128)
+    _load().oracle_overrelax(_dp(g), float(omega), int(variant), _dp(out))
+    return out

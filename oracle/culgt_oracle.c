@@ -1,0 +1,716 @@
+/*
+ * culgt oracle — a plain, slow, obviously-correct FP64 CPU restatement of
+ * lattice Landau (and Coulomb) gauge fixing by checkerboard overrelaxation,
+ * following Vogt & Schröck, "cuLGT: Lattice Gauge Fixing on GPUs"
+ * (GPUHEP2014), Sec. 2 "Lattice Gauge Fixing".
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the independent reference the CUDA
+ * library is checked against. Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline leg of bench.py may load it. It shares no code, header, table
+ * or helper with the CUDA path, and the CUDA path never calls it.
+ *
+ * Every function is pinned by tests in tests/test_oracle_pins.py against
+ * closed forms, brute force and invariants (see the header of each test).
+ *
+ * Conventions (the paper fixes none of them):
+ *   - dims L[0..3]; mu = 0 is time, mu = 1..3 are space; V = L0 L1 L2 L3.
+ *   - canonical site index i = x1 + L1 (x2 + L2 (x3 + L3 x0)).
+ *   - parity p(x) = (x0 + x1 + x2 + x3) mod 2; "black" = even, swept first.
+ *   - link buffer: double[V][4][Nc][Nc][2] (complex, re/im interleaved).
+ *   - an SU(2) element is carried as a 2x2 complex matrix everywhere here.
+ *
+ * Readings of points the paper leaves open (one line each, also listed in
+ * the design notes):
+ *   R1  SU(3) iterates the subgroups (0,1),(0,2),(1,2) once each, in that
+ *       order, and the running K is left-multiplied by each subgroup update.
+ *   R2  A 2x2 block w of K is first projected on its quaternion part
+ *       P(w) = (w + s2 conj(w) s2)/2 (s2 = Pauli sigma_2), the only part
+ *       Re tr[r w] depends on for r in SU(2); the SU(2) maximum g = K^+/sqrt(det K^+)
+ *       is then applied to P(w). For SU(2) itself K is a sum of SU(2) matrices,
+ *       so P(K) = K and this is the paper's formula as printed.
+ *   R3  g^omega is the second-order truncated binomial series
+ *       1 + w (g-1) + w(w-1)/2 (g-1)^2, rescaled back onto SU(2)
+ *       (variant 0, default); variant 1 is the exact power.
+ *   R4  det P(w) = 0 leaves the subgroup untouched (r = 1).
+ *   R5  theta = (1/V) sum_x tr[Delta(x) Delta(x)^+] with a g = 1.
+ *   R6  Coulomb: each time slice is an independent 3D Landau problem over
+ *       mu = 1..3 with its own checkerboard (black = x1+x2+x3 even); the
+ *       accumulated g(x) rotates the temporal links once at the end.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------ */
+/* complex numbers and small matrices                                  */
+/* ------------------------------------------------------------------ */
+
+typedef struct { double re, im; } cplx;
+
+static cplx c_make(double re, double im) { cplx z; z.re = re; z.im = im; return z; }
+static cplx c_add(cplx a, cplx b) { return c_make(a.re + b.re, a.im + b.im); }
+static cplx c_sub(cplx a, cplx b) { return c_make(a.re - b.re, a.im - b.im); }
+static cplx c_mul(cplx a, cplx b) { return c_make(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
+static cplx c_conj(cplx a) { return c_make(a.re, -a.im); }
+static cplx c_scale(cplx a, double s) { return c_make(a.re * s, a.im * s); }
+static double c_abs2(cplx a) { return a.re * a.re + a.im * a.im; }
+static cplx c_div(cplx a, cplx b)
+{
+    double d = c_abs2(b);
+    return c_scale(c_mul(a, c_conj(b)), 1.0 / d);
+}
+/* principal square root */
+static cplx c_sqrt(cplx z)
+{
+    double r = sqrt(c_abs2(z));
+    double re = sqrt(0.5 * (r + z.re));
+    double im = sqrt(0.5 * (r - z.re));
+    if (z.im < 0) im = -im;
+    return c_make(re, im);
+}
+
+/* n x n complex matrix, n = Nc in {2,3} (SU(2) uses the top-left 2x2). */
+typedef struct { int n; cplx m[3][3]; } mat;
+
+static mat mat_zero(int n)
+{
+    mat A;
+    memset(&A, 0, sizeof A);
+    A.n = n;
+    return A;
+}
+static mat mat_identity(int n)
+{
+    mat A = mat_zero(n);
+    for (int a = 0; a < n; a++) A.m[a][a] = c_make(1.0, 0.0);
+    return A;
+}
+static mat mat_mul(const mat *A, const mat *B)
+{
+    mat C = mat_zero(A->n);
+    for (int a = 0; a < A->n; a++)
+        for (int b = 0; b < A->n; b++) {
+            cplx s = c_make(0.0, 0.0);
+            for (int k = 0; k < A->n; k++) s = c_add(s, c_mul(A->m[a][k], B->m[k][b]));
+            C.m[a][b] = s;
+        }
+    return C;
+}
+static mat mat_adj(const mat *A)
+{
+    mat C = mat_zero(A->n);
+    for (int a = 0; a < A->n; a++)
+        for (int b = 0; b < A->n; b++) C.m[a][b] = c_conj(A->m[b][a]);
+    return C;
+}
+static mat mat_add(const mat *A, const mat *B)
+{
+    mat C = mat_zero(A->n);
+    for (int a = 0; a < A->n; a++)
+        for (int b = 0; b < A->n; b++) C.m[a][b] = c_add(A->m[a][b], B->m[a][b]);
+    return C;
+}
+static mat mat_sub(const mat *A, const mat *B)
+{
+    mat C = mat_zero(A->n);
+    for (int a = 0; a < A->n; a++)
+        for (int b = 0; b < A->n; b++) C.m[a][b] = c_sub(A->m[a][b], B->m[a][b]);
+    return C;
+}
+static mat mat_scale(const mat *A, cplx s)
+{
+    mat C = mat_zero(A->n);
+    for (int a = 0; a < A->n; a++)
+        for (int b = 0; b < A->n; b++) C.m[a][b] = c_mul(A->m[a][b], s);
+    return C;
+}
+static cplx mat_trace(const mat *A)
+{
+    cplx s = c_make(0.0, 0.0);
+    for (int a = 0; a < A->n; a++) s = c_add(s, A->m[a][a]);
+    return s;
+}
+static cplx mat_det2(const mat *A)
+{
+    return c_sub(c_mul(A->m[0][0], A->m[1][1]), c_mul(A->m[0][1], A->m[1][0]));
+}
+
+/* ------------------------------------------------------------------ */
+/* lattice geometry                                                    */
+/* ------------------------------------------------------------------ */
+
+typedef struct { int L[4]; long V; } lattice;
+
+static lattice make_lattice(const int *L)
+{
+    lattice lat;
+    for (int mu = 0; mu < 4; mu++) lat.L[mu] = L[mu];
+    lat.V = (long)L[0] * L[1] * L[2] * L[3];
+    return lat;
+}
+static void site_coords(const lattice *lat, long i, int x[4])
+{
+    x[1] = (int)(i % lat->L[1]); i /= lat->L[1];
+    x[2] = (int)(i % lat->L[2]); i /= lat->L[2];
+    x[3] = (int)(i % lat->L[3]); i /= lat->L[3];
+    x[0] = (int)i;
+}
+static long site_index(const lattice *lat, const int x[4])
+{
+    return x[1] + (long)lat->L[1] * (x[2] + (long)lat->L[2] * (x[3] + (long)lat->L[3] * x[0]));
+}
+/* the site x + step * mu-hat, periodic */
+static long site_shift(const lattice *lat, long i, int mu, int step)
+{
+    int x[4];
+    site_coords(lat, i, x);
+    x[mu] = ((x[mu] + step) % lat->L[mu] + lat->L[mu]) % lat->L[mu];
+    return site_index(lat, x);
+}
+
+static mat get_link(const double *U, int nc, long i, int mu)
+{
+    mat A = mat_zero(nc);
+    const double *p = U + ((size_t)i * 4 + mu) * nc * nc * 2;
+    for (int a = 0; a < nc; a++)
+        for (int b = 0; b < nc; b++) A.m[a][b] = c_make(p[(a * nc + b) * 2], p[(a * nc + b) * 2 + 1]);
+    return A;
+}
+static void put_link(double *U, int nc, long i, int mu, const mat *A)
+{
+    double *p = U + ((size_t)i * 4 + mu) * nc * nc * 2;
+    for (int a = 0; a < nc; a++)
+        for (int b = 0; b < nc; b++) {
+            p[(a * nc + b) * 2] = A->m[a][b].re;
+            p[(a * nc + b) * 2 + 1] = A->m[a][b].im;
+        }
+}
+static mat get_mat(const double *G, int nc, long k)
+{
+    mat A = mat_zero(nc);
+    const double *p = G + (size_t)k * nc * nc * 2;
+    for (int a = 0; a < nc; a++)
+        for (int b = 0; b < nc; b++) A.m[a][b] = c_make(p[(a * nc + b) * 2], p[(a * nc + b) * 2 + 1]);
+    return A;
+}
+static void put_mat(double *G, int nc, long k, const mat *A)
+{
+    double *p = G + (size_t)k * nc * nc * 2;
+    for (int a = 0; a < nc; a++)
+        for (int b = 0; b < nc; b++) {
+            p[(a * nc + b) * 2] = A->m[a][b].re;
+            p[(a * nc + b) * 2 + 1] = A->m[a][b].im;
+        }
+}
+
+/* ------------------------------------------------------------------ */
+/* local maximisation, Sec. 2                                          */
+/* ------------------------------------------------------------------ */
+
+/* Quaternion (real-SU(2)-span) part of a 2x2 complex matrix:
+ * P(w) = (w + s2 conj(w) s2)/2, where s2 conj(w) s2 = [[w11*, -w10*], [-w01*, w00*]].
+ * For r in SU(2), Re tr[r w] = Re tr[r P(w)]  (reading R2). */
+static mat su2_part(const mat *w)
+{
+    mat t = mat_zero(2);
+    t.m[0][0] = c_conj(w->m[1][1]);
+    t.m[0][1] = c_scale(c_conj(w->m[1][0]), -1.0);
+    t.m[1][0] = c_scale(c_conj(w->m[0][1]), -1.0);
+    t.m[1][1] = c_conj(w->m[0][0]);
+    mat s = mat_add(w, &t);
+    return mat_scale(&s, c_make(0.5, 0.0));
+}
+
+/* SU(2) local maximum of Re tr[g K]: g = K^+ / sqrt(det K^+)  (Sec. 2),
+ * applied to the quaternion part of K (R2); det = 0 gives g = 1 (R4). */
+static mat su2_local_max(const mat *K)
+{
+    mat q = su2_part(K);
+    mat qd = mat_adj(&q);
+    cplx d = mat_det2(&qd);
+    if (d.re == 0.0 && d.im == 0.0) return mat_identity(2);
+    cplx s = c_sqrt(d);
+    mat g = mat_zero(2);
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++) g.m[a][b] = c_div(qd.m[a][b], s);
+    return g;
+}
+
+/* Overrelaxation g -> g^omega, omega in [1,2)  (Sec. 2, reading R3). */
+static mat overrelax(const mat *g, double omega, int variant)
+{
+    if (variant == 0) {
+        /* 1 + w (g-1) + w(w-1)/2 (g-1)^2, then back onto SU(2): the sum is a
+         * real multiple of an SU(2) matrix, so divide by sqrt(det). */
+        mat one = mat_identity(2);
+        mat D = mat_sub(g, &one);
+        mat D2 = mat_mul(&D, &D);
+        mat t1 = mat_scale(&D, c_make(omega, 0.0));
+        mat t2 = mat_scale(&D2, c_make(0.5 * omega * (omega - 1.0), 0.0));
+        mat G = mat_add(&one, &t1);
+        G = mat_add(&G, &t2);
+        cplx s = c_sqrt(mat_det2(&G));
+        mat out = mat_zero(2);
+        for (int a = 0; a < 2; a++)
+            for (int b = 0; b < 2; b++) out.m[a][b] = c_div(G.m[a][b], s);
+        return out;
+    } else {
+        /* exact power: g = cos(phi) 1 + S with S = (g - g^+)/2 = i sin(phi) n.sigma,
+         * g^omega = cos(omega phi) 1 + sin(omega phi)/sin(phi) S. */
+        mat gd = mat_adj(g);
+        mat S = mat_sub(g, &gd);
+        S = mat_scale(&S, c_make(0.5, 0.0));
+        double cphi = 0.5 * mat_trace(g).re;
+        double sphi = sqrt(fmax(mat_det2(&S).re, 0.0));
+        if (sphi == 0.0) return *g;
+        double phi = atan2(sphi, cphi);
+        mat out = mat_scale(&S, c_make(sin(omega * phi) / sphi, 0.0));
+        out.m[0][0] = c_add(out.m[0][0], c_make(cos(omega * phi), 0.0));
+        out.m[1][1] = c_add(out.m[1][1], c_make(cos(omega * phi), 0.0));
+        return out;
+    }
+}
+
+/* The overrelaxed local gauge transformation g(x) for the gathered K(x).
+ * SU(2): g = (K^+/sqrt(det K^+))^omega.  SU(3): iterate over the SU(2)
+ * subgroups (R1), each hit maximising Re tr[r w] on its 2x2 block of the
+ * running K and then overrelaxed. */
+static mat local_gauge(const mat *K, double omega, int variant)
+{
+    int n = K->n;
+    if (n == 2) {
+        mat r = su2_local_max(K);
+        return overrelax(&r, omega, variant);
+    }
+    static const int sub[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    mat Kr = *K;
+    mat g = mat_identity(3);
+    for (int s = 0; s < 3; s++) {
+        int i = sub[s][0], j = sub[s][1];
+        mat w = mat_zero(2);
+        w.m[0][0] = Kr.m[i][i];
+        w.m[0][1] = Kr.m[i][j];
+        w.m[1][0] = Kr.m[j][i];
+        w.m[1][1] = Kr.m[j][j];
+        mat r = su2_local_max(&w);
+        r = overrelax(&r, omega, variant);
+        mat R = mat_identity(3);
+        R.m[i][i] = r.m[0][0];
+        R.m[i][j] = r.m[0][1];
+        R.m[j][i] = r.m[1][0];
+        R.m[j][j] = r.m[1][1];
+        Kr = mat_mul(&R, &Kr);
+        g = mat_mul(&R, &g);
+    }
+    return g;
+}
+
+/* ------------------------------------------------------------------ */
+/* the checkerboard sweep, Sec. 2                                      */
+/* ------------------------------------------------------------------ */
+
+/* K(x) = sum_mu [U_mu(x) + U_mu(x - mu)^+]  over mu = mu_first..3 */
+static mat gather_K(const double *U, const lattice *lat, int nc, long i, int mu_first)
+{
+    mat K = mat_zero(nc);
+    for (int mu = mu_first; mu < 4; mu++) {
+        mat f = get_link(U, nc, i, mu);
+        mat b = get_link(U, nc, site_shift(lat, i, mu, -1), mu);
+        mat bd = mat_adj(&b);
+        K = mat_add(&K, &f);
+        K = mat_add(&K, &bd);
+    }
+    return K;
+}
+
+/* One site update: U_mu(x) <- g U_mu(x), U_mu(x-mu) <- U_mu(x-mu) g^+,
+ * i.e. the gauge transformation of Sec. 2 with g = 1 at every other site. */
+static void update_site(double *U, const lattice *lat, int nc, long i, int mu_first,
+                        double omega, int variant, double *gacc)
+{
+    mat K = gather_K(U, lat, nc, i, mu_first);
+    mat g = local_gauge(&K, omega, variant);
+    mat gd = mat_adj(&g);
+    for (int mu = mu_first; mu < 4; mu++) {
+        long ib = site_shift(lat, i, mu, -1);
+        mat f = get_link(U, nc, i, mu);
+        mat b = get_link(U, nc, ib, mu);
+        mat fn = mat_mul(&g, &f);
+        mat bn = mat_mul(&b, &gd);
+        put_link(U, nc, i, mu, &fn);
+        put_link(U, nc, ib, mu, &bn);
+    }
+    if (gacc) {
+        mat a = get_mat(gacc, nc, i);
+        mat an = mat_mul(&g, &a);
+        put_mat(gacc, nc, i, &an);
+    }
+}
+
+static int site_parity(const lattice *lat, long i, int mu_first)
+{
+    int x[4];
+    site_coords(lat, i, x);
+    int p = x[1] + x[2] + x[3];
+    if (mu_first == 0) p += x[0];
+    return p & 1;
+}
+
+/* Update every site of the given parity. Same-parity sites share no link,
+ * so the order (and the thread split) does not change the result. */
+void oracle_halfsweep(double *U, const int *L, int nc, int parity, double omega, int variant)
+{
+    lattice lat = make_lattice(L);
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < lat.V; i++)
+        if (site_parity(&lat, i, 0) == parity) update_site(U, &lat, nc, i, 0, omega, variant, NULL);
+}
+
+/* One sweep = black (even) half-sweep, then white (odd). */
+void oracle_sweep(double *U, const int *L, int nc, double omega, int variant, int n_sweeps)
+{
+    for (int s = 0; s < n_sweeps; s++) {
+        oracle_halfsweep(U, L, nc, 0, omega, variant);
+        oracle_halfsweep(U, L, nc, 1, omega, variant);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* gauge precision theta and functional F, Sec. 2                      */
+/* ------------------------------------------------------------------ */
+
+/* A_mu(x) = [(U - U^+)/(2i)]_traceless   (a g = 1) */
+static mat gauge_field(const mat *U)
+{
+    int n = U->n;
+    mat Ud = mat_adj(U);
+    mat D = mat_sub(U, &Ud);
+    mat A = mat_scale(&D, c_make(0.0, -0.5)); /* 1/(2i) = -i/2 */
+    cplx tr = mat_trace(&A);
+    for (int a = 0; a < n; a++) A.m[a][a] = c_sub(A.m[a][a], c_scale(tr, 1.0 / n));
+    return A;
+}
+
+/* tr[Delta(x) Delta(x)^+], Delta(x) = sum_mu (A_mu(x) - A_mu(x - mu)), mu >= mu_first */
+static double site_theta(const double *U, const lattice *lat, int nc, long i, int mu_first)
+{
+    mat Dl = mat_zero(nc);
+    for (int mu = mu_first; mu < 4; mu++) {
+        mat f = get_link(U, nc, i, mu);
+        mat b = get_link(U, nc, site_shift(lat, i, mu, -1), mu);
+        mat Af = gauge_field(&f);
+        mat Ab = gauge_field(&b);
+        Dl = mat_add(&Dl, &Af);
+        Dl = mat_sub(&Dl, &Ab);
+    }
+    mat Dd = mat_adj(&Dl);
+    mat P = mat_mul(&Dl, &Dd);
+    return mat_trace(&P).re;
+}
+
+static double site_F(const double *U, int nc, long i, int mu_first)
+{
+    double s = 0.0;
+    for (int mu = mu_first; mu < 4; mu++) {
+        mat f = get_link(U, nc, i, mu);
+        s += mat_trace(&f).re;
+    }
+    return s;
+}
+
+/* theta = (1/V) sum_x tr[Delta Delta^+]   (R5)
+ * F     = 1/(Nd Nc V) sum_x sum_mu Re tr U_mu(x)   (Sec. 2, on the current links)
+ * Per-site values are summed in site order, so the result is deterministic. */
+void oracle_theta(const double *U, const int *L, int nc, double *theta, double *F)
+{
+    lattice lat = make_lattice(L);
+    double *th = (double *)malloc(sizeof(double) * lat.V);
+    double *ff = (double *)malloc(sizeof(double) * lat.V);
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < lat.V; i++) {
+        th[i] = site_theta(U, &lat, nc, i, 0);
+        ff[i] = site_F(U, nc, i, 0);
+    }
+    double st = 0.0, sf = 0.0;
+    for (long i = 0; i < lat.V; i++) {
+        st += th[i];
+        sf += ff[i];
+    }
+    free(th);
+    free(ff);
+    *theta = st / (double)lat.V;
+    *F = sf / (4.0 * nc * (double)lat.V);
+}
+
+/* Average plaquette (1/(6 Nc V)) sum_x sum_{mu<nu} Re tr[U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+],
+ * gauge invariant under the transformation of Sec. 2. */
+double oracle_plaquette(const double *U, const int *L, int nc)
+{
+    lattice lat = make_lattice(L);
+    double *pp = (double *)malloc(sizeof(double) * lat.V);
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < lat.V; i++) {
+        double s = 0.0;
+        for (int mu = 0; mu < 4; mu++)
+            for (int nu = mu + 1; nu < 4; nu++) {
+                mat a = get_link(U, nc, i, mu);
+                mat b = get_link(U, nc, site_shift(&lat, i, mu, 1), nu);
+                mat c = get_link(U, nc, site_shift(&lat, i, nu, 1), mu);
+                mat d = get_link(U, nc, i, nu);
+                mat cd = mat_adj(&c), dd = mat_adj(&d);
+                mat t = mat_mul(&a, &b);
+                t = mat_mul(&t, &cd);
+                t = mat_mul(&t, &dd);
+                s += mat_trace(&t).re;
+            }
+        pp[i] = s;
+    }
+    double s = 0.0;
+    for (long i = 0; i < lat.V; i++) s += pp[i];
+    free(pp);
+    return s / (6.0 * nc * (double)lat.V);
+}
+
+/* ------------------------------------------------------------------ */
+/* reunitarisation and unitarity                                       */
+/* ------------------------------------------------------------------ */
+
+/* SU(3): normalise row 0; row 1 -= (row0^+ . row1) row 0, normalise;
+ * row 2 = conj(row0 x row1). SU(2): project on the quaternion part, then
+ * divide by sqrt(det). Also the reconstruction rule of the 12-real storage
+ * (Sec. 3.1: only the first two rows are kept). */
+static mat reunitarize_one(const mat *A)
+{
+    if (A->n == 2) {
+        mat q = su2_part(A);
+        cplx s = c_sqrt(mat_det2(&q));
+        mat out = mat_zero(2);
+        for (int a = 0; a < 2; a++)
+            for (int b = 0; b < 2; b++) out.m[a][b] = c_div(q.m[a][b], s);
+        return out;
+    }
+    mat R = *A;
+    double n0 = 0.0;
+    for (int b = 0; b < 3; b++) n0 += c_abs2(R.m[0][b]);
+    n0 = 1.0 / sqrt(n0);
+    for (int b = 0; b < 3; b++) R.m[0][b] = c_scale(R.m[0][b], n0);
+    cplx ip = c_make(0.0, 0.0);
+    for (int b = 0; b < 3; b++) ip = c_add(ip, c_mul(c_conj(R.m[0][b]), R.m[1][b]));
+    for (int b = 0; b < 3; b++) R.m[1][b] = c_sub(R.m[1][b], c_mul(ip, R.m[0][b]));
+    double n1 = 0.0;
+    for (int b = 0; b < 3; b++) n1 += c_abs2(R.m[1][b]);
+    n1 = 1.0 / sqrt(n1);
+    for (int b = 0; b < 3; b++) R.m[1][b] = c_scale(R.m[1][b], n1);
+    for (int b = 0; b < 3; b++) {
+        int c = (b + 1) % 3, d = (b + 2) % 3;
+        R.m[2][b] = c_conj(c_sub(c_mul(R.m[0][c], R.m[1][d]), c_mul(R.m[0][d], R.m[1][c])));
+    }
+    return R;
+}
+
+/* in place, over n_mats consecutive Nc x Nc matrices */
+void oracle_reunitarize(double *M, long n_mats, int nc)
+{
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < n_mats; k++) {
+        mat A = get_mat(M, nc, k);
+        mat R = reunitarize_one(&A);
+        put_mat(M, nc, k, &R);
+    }
+}
+
+/* max over matrices of max_ab |(A A^+ - 1)_ab| */
+double oracle_unitarity_error(const double *M, long n_mats, int nc)
+{
+    double worst = 0.0;
+    for (long k = 0; k < n_mats; k++) {
+        mat A = get_mat(M, nc, k);
+        mat Ad = mat_adj(&A);
+        mat P = mat_mul(&A, &Ad);
+        for (int a = 0; a < nc; a++)
+            for (int b = 0; b < nc; b++) {
+                cplx e = c_sub(P.m[a][b], c_make(a == b ? 1.0 : 0.0, 0.0));
+                double v = sqrt(c_abs2(e));
+                if (v > worst) worst = v;
+            }
+    }
+    return worst;
+}
+
+/* ------------------------------------------------------------------ */
+/* the iteration to a given precision, Sec. 2                          */
+/* ------------------------------------------------------------------ */
+
+/* Landau gauge fixing: theta is measured before the first sweep and after
+ * every check_every sweeps (and at max_sweeps); the loop stops at the first
+ * measurement with theta < theta_target, or at max_sweeps. After sweep n the
+ * links are reunitarised when reunit_every > 0 and n % reunit_every == 0.
+ * Returns 0 if converged, 1 if max_sweeps was reached. */
+int oracle_landau_fix(double *U, const int *L, int nc, double omega, int variant, double theta_target,
+                      int max_sweeps, int check_every, int reunit_every, int *sweeps_out, double *theta_out,
+                      double *F_out)
+{
+    lattice lat = make_lattice(L);
+    double th, F;
+    int n = 0;
+    oracle_theta(U, L, nc, &th, &F);
+    while (!(th < theta_target) && n < max_sweeps) {
+        for (int k = 0; k < check_every && n < max_sweeps; k++) {
+            oracle_sweep(U, L, nc, omega, variant, 1);
+            n++;
+            if (reunit_every > 0 && n % reunit_every == 0) oracle_reunitarize(U, lat.V * 4, nc);
+        }
+        oracle_theta(U, L, nc, &th, &F);
+    }
+    *sweeps_out = n;
+    *theta_out = th;
+    *F_out = F;
+    return th < theta_target ? 0 : 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Coulomb gauge: one 3D Landau problem per time slice (R6)            */
+/* ------------------------------------------------------------------ */
+
+static long slice_site(const lattice *lat, int t, long j)
+{
+    return (long)t * lat->L[1] * lat->L[2] * lat->L[3] + j;
+}
+
+/* theta_t and F_t of time slice t: mu = 1..3, V3 = L1 L2 L3 */
+void oracle_theta_slice(const double *U, const int *L, int nc, int t, double *theta, double *F)
+{
+    lattice lat = make_lattice(L);
+    long V3 = (long)L[1] * L[2] * L[3];
+    double st = 0.0, sf = 0.0;
+    for (long j = 0; j < V3; j++) {
+        long i = slice_site(&lat, t, j);
+        st += site_theta(U, &lat, nc, i, 1);
+        sf += site_F(U, nc, i, 1);
+    }
+    *theta = st / (double)V3;
+    *F = sf / (3.0 * nc * (double)V3);
+}
+
+static void slice_halfsweep(double *U, const lattice *lat, int nc, int t, int parity, double omega,
+                            int variant, double *gacc)
+{
+    long V3 = (long)lat->L[1] * lat->L[2] * lat->L[3];
+#pragma omp parallel for schedule(static)
+    for (long j = 0; j < V3; j++) {
+        long i = slice_site(lat, t, j);
+        if (site_parity(lat, i, 1) == parity) update_site(U, lat, nc, i, 1, omega, variant, gacc);
+    }
+}
+
+static void slice_reunitarize(double *U, const lattice *lat, int nc, int t, double *gacc)
+{
+    long V3 = (long)lat->L[1] * lat->L[2] * lat->L[3];
+    for (long j = 0; j < V3; j++) {
+        long i = slice_site(lat, t, j);
+        for (int mu = 1; mu < 4; mu++) {
+            mat A = get_link(U, nc, i, mu);
+            mat R = reunitarize_one(&A);
+            put_link(U, nc, i, mu, &R);
+        }
+        mat G = get_mat(gacc, nc, i);
+        mat R = reunitarize_one(&G);
+        put_mat(gacc, nc, i, &R);
+    }
+}
+
+/* Coulomb gauge fixing: every slice t runs the Landau iteration above on its
+ * spatial links alone and stops at its own theta_t; the accumulated g(x) then
+ * rotates the temporal links, U_0(x) <- g(x) U_0(x) g(x+0)^+. gacc (V Nc Nc
+ * complex) receives the accumulated transformation. Per-slice outputs have
+ * L[0] entries. Returns 0 if every slice converged. */
+int oracle_coulomb_fix(double *U, const int *L, int nc, double omega, int variant, double theta_target,
+                       int max_sweeps, int check_every, int reunit_every, double *gacc, int *sweeps_t,
+                       double *theta_t, double *F_t)
+{
+    lattice lat = make_lattice(L);
+    int all_ok = 1;
+    for (long i = 0; i < lat.V; i++) {
+        mat I = mat_identity(nc);
+        put_mat(gacc, nc, i, &I);
+    }
+    for (int t = 0; t < L[0]; t++) {
+        double th, F;
+        int n = 0;
+        oracle_theta_slice(U, L, nc, t, &th, &F);
+        while (!(th < theta_target) && n < max_sweeps) {
+            for (int k = 0; k < check_every && n < max_sweeps; k++) {
+                slice_halfsweep(U, &lat, nc, t, 0, omega, variant, gacc);
+                slice_halfsweep(U, &lat, nc, t, 1, omega, variant, gacc);
+                n++;
+                if (reunit_every > 0 && n % reunit_every == 0) slice_reunitarize(U, &lat, nc, t, gacc);
+            }
+            oracle_theta_slice(U, L, nc, t, &th, &F);
+        }
+        sweeps_t[t] = n;
+        theta_t[t] = th;
+        F_t[t] = F;
+        if (!(th < theta_target)) all_ok = 0;
+    }
+    /* temporal links, read only above */
+    for (long i = 0; i < lat.V; i++) {
+        mat g = get_mat(gacc, nc, i);
+        mat gf = get_mat(gacc, nc, site_shift(&lat, i, 0, 1));
+        mat gfd = mat_adj(&gf);
+        mat u = get_link(U, nc, i, 0);
+        mat t = mat_mul(&g, &u);
+        t = mat_mul(&t, &gfd);
+        put_link(U, nc, i, 0, &t);
+    }
+    return all_ok ? 0 : 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* single-matrix entry points for the pin tests                        */
+/* ------------------------------------------------------------------ */
+
+/* g for one gathered K (Nc x Nc complex, interleaved) */
+void oracle_local_gauge(const double *K, int nc, double omega, int variant, double *g)
+{
+    mat k = get_mat(K, nc, 0);
+    mat r = local_gauge(&k, omega, variant);
+    put_mat(g, nc, 0, &r);
+}
+
+/* the SU(2) maximiser of Re tr[r w] for a 2x2 block w (no overrelaxation) */
+void oracle_su2_local_max(const double *w, double *r)
+{
+    mat a = get_mat(w, 2, 0);
+    mat b = su2_local_max(&a);
+    put_mat(r, 2, 0, &b);
+}
+
+/* g^omega for one SU(2) matrix */
+void oracle_overrelax(const double *g, double omega, int variant, double *out)
+{
+    mat a = get_mat(g, 2, 0);
+    mat b = overrelax(&a, omega, variant);
+    put_mat(out, 2, 0, &b);
+}
+
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int oracle_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
