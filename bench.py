@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Throughput of checkerboard-overrelaxation Landau gauge fixing on one GB300.
+
+Workload: SU(3), 32^4 periodic lattice, U_mu(x) = g(x) exp(i 0.3 H_mu(x)) g(x+mu)^+
+with Haar-random g (seed 2), omega = 1.7. One step is a whole gauge fixing
+through the library's handle: canonical links (resident in HBM) -> internal
+layout, FP32 12-real sweeps until theta < 1e-8, switch to FP64 18-real, FP64
+sweeps until theta < 1e-12 (theta every 10 sweeps, reunitarisation every 50),
+internal -> canonical. value = site updates per second over the K timed steps.
+
+Also reported: plain FP64 time to theta < 1e-12 on the same input, the
+end-to-end rate through culgt_landau_fix_host (host buffers, copies inside),
+the roofline of the dominant kernel (CUDA events, back-to-back launches) and
+the FP64 CPU oracle on the host cores.
+
+--impl reference times the FP64 CPU oracle instead (the only other
+implementation of the method here): each step is one oracle sweep of the same
+lattice on the host cores.
+
+Multi-GPU (torchrun): the path does not shard across GPUs here; every rank
+gauge-fixes its own replica and value sums the ranks' site updates over the
+slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SU(3) OR site-updates/s, HBM GB/s; time to θ<1e-12 mixed vs plain FP64"
+UNIT = "site-updates/s"
+
+WORKLOADS = {
+    # name: dims, nc, eps, seed, omega
+    "su3_32x32x32x32": ((32, 32, 32, 32), 3, 0.3, 2, 1.7),
+    "su3_4x4x4x4": ((4, 4, 4, 4), 3, 0.3, 1, 1.7),
+}
+
+# algorithmic bytes per site update: 8 links read + 8 written
+BYTES_PER_SITE = {(3, 1, 12): 768, (3, 1, 18): 1152, (3, 0, 18): 2304, (3, 0, 12): 1536,
+                  (2, 1, 4): 256, (2, 0, 4): 512}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="culgt", choices=["culgt", "reference"])
+    ap.add_argument("--workload", default="su3_32x32x32x32", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1412_3655_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except OSError:
+        return None
+    entry = rec.get(kernel_key)
+    if not entry or entry.get("source_hash") != source_hash():
+        return None
+    return entry.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_index):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            ids = [v.strip() for v in vis.split(",") if v.strip()]
+            self.index = ids[local_index] if local_index < len(ids) else str(local_index)
+        else:
+            self.index = str(local_index)
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) == 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(U, dims, nc, omega, budget_s=12.0):
+    """The FP64 oracle, as it stands, on the host cores: whole-lattice sweeps
+    until about budget_s seconds have passed."""
+    import oracle
+    work = U.copy()
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.sweep(work, dims, nc, omega, 1)
+        n += 1
+        if time.perf_counter() - t0 > budget_s or n >= 50:
+            break
+    dt = time.perf_counter() - t0
+    V = int(dims[0] * dims[1] * dims[2] * dims[3])
+    return {"value": n * V / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"{n} FP64 sweeps of the {'x'.join(map(str, dims))} SU({nc}) lattice ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+
+    import oracle
+    from paper_1412_3655_gb300 import synth
+    dims, nc, eps, seed, omega = WORKLOADS[args.workload]
+    oracle.build()
+    U = synth.gauge_config(dims, nc, eps, seed)
+    V = int(dims[0] * dims[1] * dims[2] * dims[3])
+    work = U.copy()
+    for _ in range(args.warmup):
+        oracle.sweep(work, dims, nc, omega, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sweep(work, dims, nc, omega, 1)
+    dt = time.perf_counter() - t0
+    value = args.steps * V / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "dims": list(dims), "nc": nc, "eps": eps, "seed": seed,
+                   "omega": omega, "step": "one FP64 oracle sweep of the whole lattice on the host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                         "sample": f"{args.steps} FP64 sweeps of the {'x'.join(map(str, dims))} lattice"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_culgt(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1412_3655_gb300 import culgt, synth
+
+    dims, nc, eps, seed, omega = WORKLOADS[args.workload]
+    V = int(dims[0] * dims[1] * dims[2] * dims[3])
+    U = synth.gauge_config(dims, nc, eps, seed)
+    host = torch.from_numpy(U.view(np.float64).copy())
+    d_in = host.to(dev)
+    d_out = torch.empty_like(d_in)
+    stream = torch.cuda.current_stream(dev)
+
+    mixed = culgt.Params.defaults(nc, dims, omega=omega, precision=culgt.MIXED, check_every=10, reunit_every=50,
+                                  max_sweeps=20000)
+    plain = culgt.Params.defaults(nc, dims, omega=omega, precision=culgt.FP64, check_every=10, reunit_every=50,
+                                  max_sweeps=20000)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    h = culgt.Handle(mixed, stream)
+
+    def step():
+        h.culgt_load(d_in)
+        r = h.culgt_handle_fix()
+        h.culgt_store(d_out)
+        return r
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = culgt.culgt_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    results = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        results.append(step())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = culgt.culgt_kernel_launches() - launches0
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    updates = sum((r.sweeps_fp32 + r.sweeps_fp64) * V for r in results)
+    value = updates * ws / (ms / 1e3)
+    last = results[-1]
+
+    # per-kernel launch times: back-to-back half-sweeps on the launching stream
+    def kernel_ms(params, n_sweeps=100):
+        with culgt.Handle(params, stream) as hk:
+            hk.culgt_load(d_in)
+            hk.culgt_handle_sweep(5)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            hk.culgt_handle_sweep(n_sweeps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / (2 * n_sweeps)
+
+    p32 = culgt.Params.defaults(nc, dims, omega=omega, precision=culgt.FP32)
+    t32 = kernel_ms(p32)
+    t64 = kernel_ms(plain, 20)
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    share32 = last.sweeps_fp32 * t32
+    share64 = last.sweeps_fp64 * t64
+
+    def roofline(key, t_ms):
+        bytes_launch = (V // 2) * BYTES_PER_SITE[key]
+        achieved = bytes_launch / (t_ms / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": recorded_traffic(f"halfsweep_su{nc}_{'f32' if key[1] else 'f64'}_{key[2]}"),
+                "kernel": f"k_halfsweep SU({nc}) {'FP32' if key[1] else 'FP64'} {key[2]}-real",
+                "launch_ms": t_ms, "algorithmic_bytes_per_launch": bytes_launch,
+                "peak_source": f"{peak_src} hbm_gbs"}
+
+    rl32 = roofline((nc, 1, 12), t32)
+    rl64 = roofline((nc, 0, 18), t64)
+    dominant = rl32 if share32 >= share64 else rl64
+
+    # plain FP64 time to theta < 1e-12 on the same input
+    hp = culgt.Handle(plain, stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    hp.culgt_load(d_in)
+    rp = hp.culgt_handle_fix()
+    hp.culgt_store(d_out)
+    b.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = a.elapsed_time(b)
+    hp.close()
+
+    # end to end through the host entry point (pinned host buffer)
+    pinned = host.pin_memory()
+    n_e2e = max(1, min(args.steps, 2))
+    culgt.culgt_landau_fix_host(pinned, mixed, stream)  # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_updates = 0
+    for _ in range(n_e2e):
+        pinned.copy_(host)
+        r = culgt.culgt_landau_fix_host(pinned, mixed, stream)
+        e2e_updates += (r.sweeps_fp32 + r.sweeps_fp64) * V
+    e2e_s = time.perf_counter() - t0
+    canon_bytes = host.numel() * host.element_size()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32->f64 (mixed)", "data": "synthetic",
+        "config": {"workload": args.workload, "dims": list(dims), "nc": nc, "eps": eps, "seed": seed,
+                   "omega": omega, "precision": "mixed: FP32 12-real to theta<1e-8, FP64 18-real to theta<1e-12",
+                   "check_every": 10, "reunit_every": 50, "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "inputs larger than L2 (FP32 links 201 MB, FP64 links 604 MB)"},
+        "sweeps": {"fp32": last.sweeps_fp32, "fp64": last.sweeps_fp64, "theta": last.theta, "F": last.F},
+        "time_to_theta": {"mixed_s": ms / args.steps / 1e3, "fp64_s": fp64_ms / 1e3,
+                          "fp64_sweeps": rp.sweeps_fp64, "fp64_F": rp.F, "mixed_F": last.F},
+        "roofline": dominant,
+        "roofline_kernels": {"fp32_12": rl32, "fp64_18": rl64},
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": canon_bytes,
+                "d2h_bytes_per_step": canon_bytes, "steps": n_e2e},
+        "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(U, dims, nc, omega)
+    h.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_culgt(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

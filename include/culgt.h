@@ -1,0 +1,162 @@
+/*
+ * culgt.h — C ABI of libculgt: lattice Landau and Coulomb gauge fixing by
+ * checkerboard overrelaxation on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is the one of Vogt & Schröck, "cuLGT: Lattice Gauge Fixing on
+ * GPUs" (GPUHEP2014), Sec. 2: every site x of one checkerboard parity gathers
+ *     K(x) = sum_mu [ U_mu(x) + U_mu(x - mu)^+ ],
+ * takes the local maximum g(x) of Re tr[g(x) K(x)] (closed form for SU(2),
+ * iterated over SU(2) subgroups for SU(3)), overrelaxes it to g^omega and
+ * applies it to the 8 links touching x; black sites, then white sites, make
+ * one sweep, iterated until the lattice Landau condition Delta(x) = 0 holds to
+ * a given precision theta.
+ *
+ * Conventions shared by every entry point
+ *   dims[4]   L0 = time extent, L1..L3 = spatial extents; every extent even
+ *             and >= 2 (the checkerboard needs it), V = L0 L1 L2 L3 < 2^29.
+ *   site      i = x1 + L1 (x2 + L2 (x3 + L3 x0)) (x1 fastest, time slowest).
+ *   parity    p(x) = (x0 + x1 + x2 + x3) mod 2, black = even, swept first.
+ *   links     canonical layout [V][4][Nc][Nc] complex, re/im interleaved,
+ *             double (dtype_in = 0) or float (dtype_in = 1), in DEVICE memory
+ *             owned by the caller, unless an entry point says "host".
+ *   theta     (1/V) sum_x tr[Delta(x) Delta(x)^+],
+ *             Delta(x) = sum_mu [A_mu(x) - A_mu(x - mu)],
+ *             A_mu = [(U_mu - U_mu^+)/(2i)]_traceless   (Sec. 2, with a g = 1).
+ *   F         1/(4 Nc V) sum_x sum_mu Re tr U_mu(x)      (Sec. 2, Landau functional).
+ *   Coulomb   each time slice t is its own 3D problem over mu = 1..3, with
+ *             theta_t, F_t normalised by V3 = L1 L2 L3 and its own
+ *             checkerboard (black = x1 + x2 + x3 even).
+ *
+ * Errors: every function returns a culgt_status and throws nothing. Arguments
+ * are validated before any device work. A CUDA error maps to CULGT_ERR_CUDA;
+ * the library never prints. Work is ordered on the caller's stream (NULL =
+ * legacy default stream); calls that return scalars (theta, F, results)
+ * synchronise that stream before returning.
+ */
+#ifndef CULGT_H
+#define CULGT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CULGT_OK = 0,
+    CULGT_NOT_CONVERGED = 1,  /* max_sweeps reached before theta < theta_target */
+    CULGT_ERR_ARG = -1,       /* NULL pointer, omega outside [1,2), bad counts ... */
+    CULGT_ERR_DIMS = -2,      /* an extent odd or < 2, or V too large */
+    CULGT_ERR_NC = -3,        /* nc not 2 or 3, or storage_reals not valid for nc */
+    CULGT_ERR_CUDA = -4,      /* a CUDA runtime call failed */
+    CULGT_ERR_OOM = -5,       /* device allocation failed */
+    CULGT_ERR_NONFINITE = -6, /* theta or F came out NaN/Inf (corrupt links) */
+    CULGT_ERR_TIMEOUT = -7    /* a bounded device-side wait gave up */
+} culgt_status;
+
+typedef enum { CULGT_FP64 = 0, CULGT_FP32 = 1, CULGT_MIXED = 2 } culgt_precision;
+
+typedef struct {
+    int dims[4];         /* L0 (time), L1, L2, L3; all even, >= 2 */
+    int nc;              /* 2 = SU(2), 3 = SU(3) */
+    double omega;        /* overrelaxation parameter, 1 <= omega < 2 (Sec. 2) */
+    int or_variant;      /* g^omega: 0 = binomial series to second order (default), 1 = exact power */
+    int precision;       /* culgt_precision */
+    int storage_reals;   /* reals per link kept in device memory: SU(3) 18 or 12 (first two rows,
+                            third rebuilt, Sec. 3.1), SU(2) 4 (quaternion); 0 = default
+                            (SU(3): 18 for FP64, 12 for FP32/mixed phase 1; SU(2): 4) */
+    double theta_target; /* stop once theta < theta_target */
+    int max_sweeps;      /* total sweep budget (both phases of the mixed schedule) */
+    int check_every;     /* theta is measured before the first sweep and every check_every sweeps */
+    int reunit_every;    /* reunitarise after sweep n when n % reunit_every == 0; 0 = never */
+    double switch_theta; /* mixed: leave the FP32 phase once theta < switch_theta */
+    int dtype_in;        /* canonical link buffer element type: 0 = double, 1 = float */
+} culgt_params;
+
+typedef struct {
+    int sweeps_fp32;      /* sweeps done with FP32 links */
+    int sweeps_fp64;      /* sweeps done with FP64 links */
+    double theta;         /* final theta */
+    double F;             /* final functional */
+    double plaq_before;   /* average plaquette of the input */
+    double plaq_after;    /* average plaquette of the output (gauge invariant: should not move) */
+    double unitarity_err; /* max_ab |(U U^+ - 1)_ab| over the output links */
+    double seconds;       /* wall time of the call */
+} culgt_result;
+
+typedef struct culgt_handle culgt_handle;
+
+/* ---- host-only helpers (no device work) ------------------------------- */
+
+/* Human-readable name of a status code. Never NULL. */
+const char *culgt_status_string(int status);
+
+/* Fills *out with the library defaults for an SU(nc) lattice of the given
+ * dims (omega 1.7, FP64, theta_target 1e-12, max_sweeps 10000, check_every
+ * 10, reunit_every 100, switch_theta 1e-8, dtype_in 0). */
+culgt_status culgt_default_params(int nc, const int dims[4], culgt_params *out);
+
+/* Validates a parameter block without touching the device. */
+culgt_status culgt_validate(const culgt_params *p);
+
+/* Number of kernels this library has launched in this process so far
+ * (diagnostic; counted on the host at each launch). */
+long long culgt_kernel_launches(void);
+
+/* Device bytes a handle for these parameters allocates. */
+culgt_status culgt_workspace_bytes(const culgt_params *p, size_t *bytes);
+
+/* ---- handle API (the hot loop; internal checkerboard layout) -----------
+ * A handle owns the links in the internal checkerboard structure-of-arrays
+ * layout (Sec. 3.1: parities split, site index fastest), plus reduction
+ * scratch. It is bound to one stream and must not be used from two host
+ * threads at once. */
+
+culgt_status culgt_create(const culgt_params *p, void *cuda_stream, culgt_handle **out);
+void culgt_destroy(culgt_handle *h);
+
+/* canonical device buffer -> internal layout of the handle's starting
+ * precision (FP32 for CULGT_FP32 and CULGT_MIXED, FP64 otherwise). */
+culgt_status culgt_load(culgt_handle *h, const void *d_links);
+/* internal layout -> canonical device buffer (dtype_in), current precision. */
+culgt_status culgt_store(culgt_handle *h, void *d_links);
+/* n_sweeps x (black half-sweep, white half-sweep), no theta, no reunitarisation. */
+culgt_status culgt_handle_sweep(culgt_handle *h, int n_sweeps);
+/* theta and F of the current links (FP64 accumulation). */
+culgt_status culgt_handle_theta(culgt_handle *h, double *theta, double *F);
+culgt_status culgt_handle_plaquette(culgt_handle *h, double *plaq);
+culgt_status culgt_handle_reunitarize(culgt_handle *h);
+/* Converts FP32 links to FP64 (third row rebuilt, FP64 reunitarisation). */
+culgt_status culgt_handle_to_fp64(culgt_handle *h);
+/* Iterates to theta_target as the precision field says (mixed: FP32 until
+ * theta < switch_theta, then FP64). Leaves the result in the handle. */
+culgt_status culgt_handle_fix(culgt_handle *h, culgt_result *out);
+
+/* ---- one-call API (allocates and frees a handle inside) ---------------- */
+
+/* Landau gauge fixing of d_links in place. out may be NULL. Returns
+ * CULGT_NOT_CONVERGED (with the links still written back) if max_sweeps ran out. */
+culgt_status culgt_landau_fix(void *d_links, const culgt_params *p, void *cuda_stream, culgt_result *out);
+
+/* Same, on a HOST buffer (pageable or pinned): host -> device copy, fix,
+ * device -> host copy, all inside the call. */
+culgt_status culgt_landau_fix_host(void *h_links, const culgt_params *p, void *cuda_stream, culgt_result *out);
+
+/* n_sweeps sweeps of d_links in place at the given precision. */
+culgt_status culgt_sweep(void *d_links, const culgt_params *p, int n_sweeps, void *cuda_stream);
+
+/* theta and F of d_links (either pointer may be NULL). */
+culgt_status culgt_theta(const void *d_links, const culgt_params *p, void *cuda_stream, double *theta, double *F);
+
+/* Average plaquette (1/(6 Nc V)) sum_x sum_{mu<nu} Re tr[U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+]. */
+culgt_status culgt_plaquette(const void *d_links, const culgt_params *p, void *cuda_stream, double *plaq);
+
+/* Reunitarisation of d_links in place (SU(3): Gram-Schmidt on rows 0, 1,
+ * row 2 = conj(row0 x row1); SU(2): normalised quaternion part). */
+culgt_status culgt_reunitarize(void *d_links, const culgt_params *p, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CULGT_H */

@@ -1,0 +1,481 @@
+// The C ABI of libculgt (include/culgt.h): argument checks, the handle, and
+// the host drivers of the iteration of Sec. 2 (half-sweeps, theta checks,
+// reunitarisation, the FP32 -> FP64 schedule).
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/culgt.h"
+#include "launch.h"
+
+using namespace culgt;
+
+struct culgt_handle {
+    culgt_params prm;
+    cudaStream_t stream;
+    Geom geom;
+    const Ops *ops32;  // FP32 storage (FP32 and mixed), else null
+    const Ops *ops64;  // FP64 storage (FP64 and mixed), else null
+    void *buf32;
+    void *buf64;
+    int cur32;         // 1 while the FP32 buffer holds the current links
+    int loaded;
+    double2 *partials;
+    double *d_scalars;  // 4 doubles
+    double *h_scalars;  // pinned, 4 doubles
+    void *staging;      // canonical device buffer for the host entry point
+    int sweeps32, sweeps64;
+};
+
+namespace {
+
+#define CU(call)                                        \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) {                        \
+            (void)cudaGetLastError();                   \
+            return CULGT_ERR_CUDA;                      \
+        }                                               \
+    } while (0)
+
+#define ST(call)                                        \
+    do {                                                \
+        culgt_status s_ = (call);                       \
+        if (s_ < 0) return s_;                          \
+    } while (0)
+
+int default_storage(int nc, int fp32) { return nc == 2 ? 4 : (fp32 ? 12 : 18); }
+
+culgt_status validate(const culgt_params *p)
+{
+    if (!p) return CULGT_ERR_ARG;
+    if (p->nc != 2 && p->nc != 3) return CULGT_ERR_NC;
+    long long V = 1;
+    for (int mu = 0; mu < 4; mu++) {
+        if (p->dims[mu] < 2 || (p->dims[mu] & 1)) return CULGT_ERR_DIMS;
+        V *= p->dims[mu];
+    }
+    if (V >= (1LL << 31) / 4) return CULGT_ERR_DIMS;
+    if (!(p->omega >= 1.0 && p->omega < 2.0)) return CULGT_ERR_ARG;
+    if (p->or_variant != 0 && p->or_variant != 1) return CULGT_ERR_ARG;
+    if (p->precision < CULGT_FP64 || p->precision > CULGT_MIXED) return CULGT_ERR_ARG;
+    if (p->nc == 3 && p->storage_reals != 0 && p->storage_reals != 12 && p->storage_reals != 18) return CULGT_ERR_NC;
+    if (p->nc == 2 && p->storage_reals != 0 && p->storage_reals != 4) return CULGT_ERR_NC;
+    if (!(p->theta_target >= 0.0) || std::isinf(p->theta_target)) return CULGT_ERR_ARG;
+    if (p->max_sweeps < 0 || p->check_every < 1 || p->reunit_every < 0) return CULGT_ERR_ARG;
+    if (p->precision == CULGT_MIXED && !(p->switch_theta > 0.0)) return CULGT_ERR_ARG;
+    if (p->dtype_in != 0 && p->dtype_in != 1) return CULGT_ERR_ARG;
+    return CULGT_OK;
+}
+
+Geom make_geom(const int *dims)
+{
+    Geom g;
+    for (int mu = 0; mu < 4; mu++) g.L[mu] = dims[mu];
+    g.half1 = dims[1] / 2;
+    g.V = dims[0] * dims[1] * dims[2] * dims[3];
+    g.Vh = g.V / 2;
+    g.stride = ((size_t)g.Vh + 63) / 64 * 64;
+    return g;
+}
+
+size_t buffer_bytes(const Ops *o, const Geom &g) { return (size_t)8 * o->nchunk * g.stride * o->chunk_bytes; }
+
+void pick_ops(const culgt_params *p, const Ops **o32, const Ops **o64)
+{
+    *o32 = *o64 = nullptr;
+    if (p->precision == CULGT_FP64) {
+        *o64 = get_ops(p->nc, 0, p->storage_reals ? p->storage_reals : default_storage(p->nc, 0));
+    } else if (p->precision == CULGT_FP32) {
+        *o32 = get_ops(p->nc, 1, p->storage_reals ? p->storage_reals : default_storage(p->nc, 1));
+    } else {
+        *o32 = get_ops(p->nc, 1, p->storage_reals ? p->storage_reals : default_storage(p->nc, 1));
+        *o64 = get_ops(p->nc, 0, default_storage(p->nc, 0));
+    }
+}
+
+size_t canonical_bytes(const culgt_params *p, const Geom &g)
+{
+    return (size_t)g.V * 4 * p->nc * p->nc * 2 * (p->dtype_in ? sizeof(float) : sizeof(double));
+}
+
+const Ops *cur_ops(const culgt_handle *h) { return h->cur32 ? h->ops32 : h->ops64; }
+void *cur_buf(const culgt_handle *h) { return h->cur32 ? h->buf32 : h->buf64; }
+
+culgt_status sync_scalars(culgt_handle *h, int n)
+{
+    CU(cudaMemcpyAsync(h->h_scalars, h->d_scalars, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    CU(cudaGetLastError());
+    return CULGT_OK;
+}
+
+// theta and F of the current links, normalised as in the header (Landau)
+culgt_status theta_now(culgt_handle *h, double *theta, double *F)
+{
+    const Geom &g = h->geom;
+    int nb = cur_ops(h)->theta_partials(cur_buf(h), g, 0, h->partials, h->stream);
+    launch_finalize2(h->partials, nb, 1.0 / g.V, 1.0 / (4.0 * h->prm.nc * g.V), h->d_scalars, h->stream);
+    ST(sync_scalars(h, 2));
+    *theta = h->h_scalars[0];
+    *F = h->h_scalars[1];
+    if (!std::isfinite(*theta) || !std::isfinite(*F)) return CULGT_ERR_NONFINITE;
+    return CULGT_OK;
+}
+
+culgt_status plaquette_now(culgt_handle *h, double *P)
+{
+    const Geom &g = h->geom;
+    int nb = cur_ops(h)->plaq_partials(cur_buf(h), g, h->partials, h->stream);
+    launch_finalize2(h->partials, nb, 1.0 / (6.0 * h->prm.nc * g.V), 0.0, h->d_scalars, h->stream);
+    ST(sync_scalars(h, 1));
+    *P = h->h_scalars[0];
+    return CULGT_OK;
+}
+
+culgt_status unitarity_now(culgt_handle *h, double *err)
+{
+    int nb = cur_ops(h)->unitarity_partials(cur_buf(h), h->geom, h->partials, h->stream);
+    launch_finalize_max(h->partials, nb, h->d_scalars, h->stream);
+    ST(sync_scalars(h, 1));
+    *err = h->h_scalars[0];
+    return CULGT_OK;
+}
+
+void sweep_now(culgt_handle *h, int n)
+{
+    const Ops *o = cur_ops(h);
+    void *b = cur_buf(h);
+    for (int k = 0; k < n; k++) {
+        o->halfsweep(b, h->geom, 0, h->prm.omega, h->prm.or_variant, h->stream);
+        o->halfsweep(b, h->geom, 1, h->prm.omega, h->prm.or_variant, h->stream);
+    }
+}
+
+// Sweeps the current links until theta < target or the running total n
+// reaches max_sweeps; theta is measured first and every check_every sweeps.
+culgt_status run_phase(culgt_handle *h, double target, int *n, int *phase_sweeps, double *theta, double *F)
+{
+    const culgt_params &p = h->prm;
+    ST(theta_now(h, theta, F));
+    while (!(*theta < target) && *n < p.max_sweeps) {
+        int k = p.check_every;
+        if (k > p.max_sweeps - *n) k = p.max_sweeps - *n;
+        for (int j = 0; j < k; j++) {
+            sweep_now(h, 1);
+            ++*n;
+            ++*phase_sweeps;
+            if (p.reunit_every > 0 && *n % p.reunit_every == 0) cur_ops(h)->reunitarize(cur_buf(h), h->geom, h->stream);
+        }
+        ST(theta_now(h, theta, F));
+    }
+    return CULGT_OK;
+}
+
+culgt_status fix_handle(culgt_handle *h, culgt_result *out)
+{
+    if (!h->loaded) return CULGT_ERR_ARG;
+    const culgt_params &p = h->prm;
+    double theta = 0.0, F = 0.0;
+    int n = 0;
+    h->sweeps32 = h->sweeps64 = 0;
+    if (p.precision == CULGT_MIXED && h->cur32) {
+        ST(run_phase(h, p.switch_theta, &n, &h->sweeps32, &theta, &F));
+        ST(culgt_handle_to_fp64(h));
+    }
+    ST(run_phase(h, p.theta_target, &n, h->cur32 ? &h->sweeps32 : &h->sweeps64, &theta, &F));
+    if (out) {
+        out->sweeps_fp32 = h->sweeps32;
+        out->sweeps_fp64 = h->sweeps64;
+        out->theta = theta;
+        out->F = F;
+    }
+    return theta < p.theta_target ? CULGT_OK : CULGT_NOT_CONVERGED;
+}
+
+struct HandleGuard {
+    culgt_handle *h = nullptr;
+    ~HandleGuard() { culgt_destroy(h); }
+};
+
+double now_seconds()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// load, fix, diagnostics, store: the body of the one-call entry points
+culgt_status fix_call(culgt_handle *h, const void *d_in, void *d_out, culgt_result *out, double t0)
+{
+    culgt_result r;
+    std::memset(&r, 0, sizeof r);
+    ST(culgt_load(h, d_in));
+    ST(plaquette_now(h, &r.plaq_before));
+    culgt_status st = fix_handle(h, &r);
+    if (st < 0) return st;
+    ST(plaquette_now(h, &r.plaq_after));
+    ST(unitarity_now(h, &r.unitarity_err));
+    ST(culgt_store(h, d_out));
+    CU(cudaStreamSynchronize(h->stream));
+    r.seconds = now_seconds() - t0;
+    if (out) *out = r;
+    return st;
+}
+
+} // namespace
+
+extern "C" {
+
+const char *culgt_status_string(int status)
+{
+    switch (status) {
+    case CULGT_OK: return "CULGT_OK";
+    case CULGT_NOT_CONVERGED: return "CULGT_NOT_CONVERGED: max_sweeps reached before theta < theta_target";
+    case CULGT_ERR_ARG: return "CULGT_ERR_ARG: invalid argument";
+    case CULGT_ERR_DIMS: return "CULGT_ERR_DIMS: every lattice extent must be even and >= 2, V < 2^29";
+    case CULGT_ERR_NC: return "CULGT_ERR_NC: nc must be 2 or 3 with a storage_reals valid for it";
+    case CULGT_ERR_CUDA: return "CULGT_ERR_CUDA: a CUDA runtime call failed";
+    case CULGT_ERR_OOM: return "CULGT_ERR_OOM: device allocation failed";
+    case CULGT_ERR_NONFINITE: return "CULGT_ERR_NONFINITE: theta or F is not finite";
+    case CULGT_ERR_TIMEOUT: return "CULGT_ERR_TIMEOUT: a bounded device-side wait gave up";
+    default: return "unknown culgt status";
+    }
+}
+
+culgt_status culgt_default_params(int nc, const int dims[4], culgt_params *out)
+{
+    if (!out || !dims) return CULGT_ERR_ARG;
+    std::memset(out, 0, sizeof *out);
+    for (int mu = 0; mu < 4; mu++) out->dims[mu] = dims[mu];
+    out->nc = nc;
+    out->omega = 1.7;
+    out->or_variant = 0;
+    out->precision = CULGT_FP64;
+    out->storage_reals = 0;
+    out->theta_target = 1e-12;
+    out->max_sweeps = 10000;
+    out->check_every = 10;
+    out->reunit_every = 100;
+    out->switch_theta = 1e-8;
+    out->dtype_in = 0;
+    return validate(out);
+}
+
+culgt_status culgt_validate(const culgt_params *p) { return validate(p); }
+
+long long culgt_kernel_launches(void) { return launches_so_far(); }
+
+culgt_status culgt_workspace_bytes(const culgt_params *p, size_t *bytes)
+{
+    ST(validate(p));
+    if (!bytes) return CULGT_ERR_ARG;
+    Geom g = make_geom(p->dims);
+    const Ops *o32, *o64;
+    pick_ops(p, &o32, &o64);
+    size_t b = (size_t)max_partials(g) * sizeof(double2) + 4 * sizeof(double);
+    if (o32) b += buffer_bytes(o32, g);
+    if (o64) b += buffer_bytes(o64, g);
+    *bytes = b;
+    return CULGT_OK;
+}
+
+culgt_status culgt_create(const culgt_params *p, void *cuda_stream, culgt_handle **out)
+{
+    ST(validate(p));
+    if (!out) return CULGT_ERR_ARG;
+    *out = nullptr;
+    culgt_handle *h = new (std::nothrow) culgt_handle;
+    if (!h) return CULGT_ERR_OOM;
+    std::memset(h, 0, sizeof *h);
+    h->prm = *p;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->geom = make_geom(p->dims);
+    pick_ops(p, &h->ops32, &h->ops64);
+    h->cur32 = h->ops32 != nullptr;
+    culgt_status st = CULGT_OK;
+    if (h->ops32 && cudaMalloc(&h->buf32, buffer_bytes(h->ops32, h->geom)) != cudaSuccess) st = CULGT_ERR_OOM;
+    if (st == CULGT_OK && h->ops64 && cudaMalloc(&h->buf64, buffer_bytes(h->ops64, h->geom)) != cudaSuccess)
+        st = CULGT_ERR_OOM;
+    if (st == CULGT_OK &&
+        cudaMalloc((void **)&h->partials, (size_t)max_partials(h->geom) * sizeof(double2)) != cudaSuccess)
+        st = CULGT_ERR_OOM;
+    if (st == CULGT_OK && cudaMalloc((void **)&h->d_scalars, 4 * sizeof(double)) != cudaSuccess) st = CULGT_ERR_OOM;
+    if (st == CULGT_OK && cudaMallocHost((void **)&h->h_scalars, 4 * sizeof(double)) != cudaSuccess)
+        st = CULGT_ERR_OOM;
+    if (st != CULGT_OK) {
+        (void)cudaGetLastError();
+        culgt_destroy(h);
+        return st;
+    }
+    *out = h;
+    return CULGT_OK;
+}
+
+void culgt_destroy(culgt_handle *h)
+{
+    if (!h) return;
+    if (h->buf32) cudaFree(h->buf32);
+    if (h->buf64) cudaFree(h->buf64);
+    if (h->partials) cudaFree(h->partials);
+    if (h->d_scalars) cudaFree(h->d_scalars);
+    if (h->h_scalars) cudaFreeHost(h->h_scalars);
+    if (h->staging) cudaFree(h->staging);
+    delete h;
+}
+
+culgt_status culgt_load(culgt_handle *h, const void *d_links)
+{
+    if (!h || !d_links) return CULGT_ERR_ARG;
+    h->cur32 = h->ops32 != nullptr;
+    const Ops *o = cur_ops(h);
+    if (h->prm.dtype_in)
+        o->to_internal_f((const float *)d_links, cur_buf(h), h->geom, h->stream);
+    else
+        o->to_internal_d((const double *)d_links, cur_buf(h), h->geom, h->stream);
+    CU(cudaGetLastError());
+    h->loaded = 1;
+    return CULGT_OK;
+}
+
+culgt_status culgt_store(culgt_handle *h, void *d_links)
+{
+    if (!h || !d_links || !h->loaded) return CULGT_ERR_ARG;
+    const Ops *o = cur_ops(h);
+    if (h->prm.dtype_in)
+        o->to_canonical_f(cur_buf(h), (float *)d_links, h->geom, h->stream);
+    else
+        o->to_canonical_d(cur_buf(h), (double *)d_links, h->geom, h->stream);
+    CU(cudaGetLastError());
+    return CULGT_OK;
+}
+
+culgt_status culgt_handle_sweep(culgt_handle *h, int n_sweeps)
+{
+    if (!h || !h->loaded || n_sweeps < 0) return CULGT_ERR_ARG;
+    sweep_now(h, n_sweeps);
+    CU(cudaGetLastError());
+    return CULGT_OK;
+}
+
+culgt_status culgt_handle_theta(culgt_handle *h, double *theta, double *F)
+{
+    if (!h || !h->loaded) return CULGT_ERR_ARG;
+    double t, f;
+    culgt_status st = theta_now(h, &t, &f);
+    if (theta) *theta = t;
+    if (F) *F = f;
+    return st;
+}
+
+culgt_status culgt_handle_plaquette(culgt_handle *h, double *plaq)
+{
+    if (!h || !h->loaded || !plaq) return CULGT_ERR_ARG;
+    return plaquette_now(h, plaq);
+}
+
+culgt_status culgt_handle_reunitarize(culgt_handle *h)
+{
+    if (!h || !h->loaded) return CULGT_ERR_ARG;
+    cur_ops(h)->reunitarize(cur_buf(h), h->geom, h->stream);
+    CU(cudaGetLastError());
+    return CULGT_OK;
+}
+
+culgt_status culgt_handle_to_fp64(culgt_handle *h)
+{
+    if (!h || !h->loaded) return CULGT_ERR_ARG;
+    if (!h->cur32) return CULGT_OK;
+    if (!h->ops64) return CULGT_ERR_ARG;  // an FP32-only handle has no FP64 buffer
+    launch_widen(h->ops32, h->buf32, h->ops64, h->buf64, h->geom, h->stream);
+    CU(cudaGetLastError());
+    h->cur32 = 0;
+    return CULGT_OK;
+}
+
+culgt_status culgt_handle_fix(culgt_handle *h, culgt_result *out)
+{
+    if (!h) return CULGT_ERR_ARG;
+    return fix_handle(h, out);
+}
+
+culgt_status culgt_landau_fix(void *d_links, const culgt_params *p, void *cuda_stream, culgt_result *out)
+{
+    double t0 = now_seconds();
+    ST(validate(p));
+    if (!d_links) return CULGT_ERR_ARG;
+    HandleGuard g;
+    ST(culgt_create(p, cuda_stream, &g.h));
+    return fix_call(g.h, d_links, d_links, out, t0);
+}
+
+culgt_status culgt_landau_fix_host(void *h_links, const culgt_params *p, void *cuda_stream, culgt_result *out)
+{
+    double t0 = now_seconds();
+    ST(validate(p));
+    if (!h_links) return CULGT_ERR_ARG;
+    HandleGuard g;
+    ST(culgt_create(p, cuda_stream, &g.h));
+    culgt_handle *h = g.h;
+    size_t bytes = canonical_bytes(p, h->geom);
+    if (cudaMalloc(&h->staging, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        h->staging = nullptr;
+        return CULGT_ERR_OOM;
+    }
+    CU(cudaMemcpyAsync(h->staging, h_links, bytes, cudaMemcpyHostToDevice, h->stream));
+    culgt_status st = fix_call(h, h->staging, h->staging, out, t0);
+    if (st < 0) return st;
+    CU(cudaMemcpyAsync(h_links, h->staging, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    if (out) out->seconds = now_seconds() - t0;
+    return st;
+}
+
+culgt_status culgt_sweep(void *d_links, const culgt_params *p, int n_sweeps, void *cuda_stream)
+{
+    ST(validate(p));
+    if (!d_links || n_sweeps < 0) return CULGT_ERR_ARG;
+    HandleGuard g;
+    ST(culgt_create(p, cuda_stream, &g.h));
+    ST(culgt_load(g.h, d_links));
+    ST(culgt_handle_sweep(g.h, n_sweeps));
+    ST(culgt_store(g.h, d_links));
+    CU(cudaStreamSynchronize(g.h->stream));
+    return CULGT_OK;
+}
+
+culgt_status culgt_theta(const void *d_links, const culgt_params *p, void *cuda_stream, double *theta, double *F)
+{
+    ST(validate(p));
+    if (!d_links) return CULGT_ERR_ARG;
+    HandleGuard g;
+    ST(culgt_create(p, cuda_stream, &g.h));
+    ST(culgt_load(g.h, d_links));
+    return culgt_handle_theta(g.h, theta, F);
+}
+
+culgt_status culgt_plaquette(const void *d_links, const culgt_params *p, void *cuda_stream, double *plaq)
+{
+    ST(validate(p));
+    if (!d_links || !plaq) return CULGT_ERR_ARG;
+    HandleGuard g;
+    ST(culgt_create(p, cuda_stream, &g.h));
+    ST(culgt_load(g.h, d_links));
+    return plaquette_now(g.h, plaq);
+}
+
+culgt_status culgt_reunitarize(void *d_links, const culgt_params *p, void *cuda_stream)
+{
+    ST(validate(p));
+    if (!d_links) return CULGT_ERR_ARG;
+    HandleGuard g;
+    ST(culgt_create(p, cuda_stream, &g.h));
+    ST(culgt_load(g.h, d_links));
+    ST(culgt_handle_reunitarize(g.h));
+    ST(culgt_store(g.h, d_links));
+    CU(cudaStreamSynchronize(g.h->stream));
+    return CULGT_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,488 @@
+// Device-side building blocks of libculgt: lattice geometry of the
+// checkerboard layout, register link types, the storage parameterisations
+// (the paper's GlobalLink/LocalLink split, Sec. 3.1) and the local
+// overrelaxation update of Sec. 2.
+//
+// Internal layout. The links of parity p, direction mu are stored as NCHUNK
+// planes of 16-byte (or 8-byte) chunks, each plane holding one chunk per
+// checkerboard site:
+//     chunk c of U_mu(x) at  base[((p * 4 + mu) * NCHUNK + c) * stride + cb(x)]
+// with cb(x) = (x1 >> 1) + (L1/2) (x2 + L2 (x3 + L3 x0)) and stride = Vh
+// rounded up to 64. Consecutive threads take consecutive cb, so every chunk
+// load and store of a warp is one contiguous 512-byte (or 256-byte) run
+// (Sec. 3.1: parities split, site index fastest; 128-bit vector elements).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace culgt {
+
+struct Geom {
+    int L[4];        // L0 = time, L1..L3 space
+    int half1;       // L1 / 2
+    int V;           // sites
+    int Vh;          // sites per parity
+    size_t stride;   // chunks per plane (Vh rounded up to 64)
+};
+
+__host__ __device__ inline int cb_index(const Geom &g, const int x[4])
+{
+    return (x[1] >> 1) + g.half1 * (x[2] + g.L[2] * (x[3] + g.L[3] * x[0]));
+}
+
+// coordinates of the parity-p site with checkerboard index cb
+__device__ inline void decode_site(const Geom &g, int cb, int p, int x[4])
+{
+    int r = cb / g.half1;
+    int x1h = cb - r * g.half1;
+    int r2 = r / g.L[2];
+    x[2] = r - r2 * g.L[2];
+    int r3 = r2 / g.L[3];
+    x[3] = r2 - r3 * g.L[3];
+    x[0] = r3;
+    x[1] = 2 * x1h + ((p + x[0] + x[2] + x[3]) & 1);
+}
+
+// checkerboard index of x + step * mu-hat (periodic); the parity flips
+__device__ __forceinline__ int cb_shift(const Geom &g, const int x[4], int mu, int step)
+{
+    int y0 = x[0], y1 = x[1], y2 = x[2], y3 = x[3];
+    int v, Lm;
+    switch (mu) {
+    case 0: v = y0; Lm = g.L[0]; break;
+    case 1: v = y1; Lm = g.L[1]; break;
+    case 2: v = y2; Lm = g.L[2]; break;
+    default: v = y3; Lm = g.L[3]; break;
+    }
+    v += step;
+    if (v < 0) v += Lm;
+    else if (v >= Lm) v -= Lm;
+    switch (mu) {
+    case 0: y0 = v; break;
+    case 1: y1 = v; break;
+    case 2: y2 = v; break;
+    default: y3 = v; break;
+    }
+    return (y1 >> 1) + g.half1 * (y2 + g.L[2] * (y3 + g.L[3] * y0));
+}
+
+__host__ __device__ inline size_t plane_offset(const Geom &g, int p, int mu, int nchunk)
+{
+    return (size_t)((p * 4 + mu) * nchunk) * g.stride;
+}
+
+// ---------------------------------------------------------------------------
+// register link types
+
+template <typename T> struct M3 {
+    T re[3][3];
+    T im[3][3];
+};
+
+// SU(2) element a0 + i (a1 s1 + a2 s2 + a3 s3) (s = Pauli matrices), i.e. the
+// 2x2 matrix [[a0 + i a3, a2 + i a1], [-a2 + i a1, a0 - i a3]]
+template <typename T> struct Q4 {
+    T a[4];
+};
+
+template <typename T> __device__ __forceinline__ void m3_zero(M3<T> &a)
+{
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) a.re[i][j] = a.im[i][j] = T(0);
+}
+
+template <typename T> __device__ __forceinline__ void m3_identity(M3<T> &a)
+{
+    m3_zero(a);
+#pragma unroll
+    for (int i = 0; i < 3; i++) a.re[i][i] = T(1);
+}
+
+// acc += u
+template <typename T> __device__ __forceinline__ void m3_acc(M3<T> &acc, const M3<T> &u)
+{
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            acc.re[i][j] += u.re[i][j];
+            acc.im[i][j] += u.im[i][j];
+        }
+}
+
+// acc += u^+
+template <typename T> __device__ __forceinline__ void m3_acc_adj(M3<T> &acc, const M3<T> &u)
+{
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            acc.re[i][j] += u.re[j][i];
+            acc.im[i][j] -= u.im[j][i];
+        }
+}
+
+// c = a b
+template <typename T> __device__ __forceinline__ void m3_mul(M3<T> &c, const M3<T> &a, const M3<T> &b)
+{
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            T sr = a.re[i][0] * b.re[0][j] - a.im[i][0] * b.im[0][j];
+            T si = a.re[i][0] * b.im[0][j] + a.im[i][0] * b.re[0][j];
+#pragma unroll
+            for (int k = 1; k < 3; k++) {
+                sr += a.re[i][k] * b.re[k][j] - a.im[i][k] * b.im[k][j];
+                si += a.re[i][k] * b.im[k][j] + a.im[i][k] * b.re[k][j];
+            }
+            c.re[i][j] = sr;
+            c.im[i][j] = si;
+        }
+}
+
+// c = a b^+
+template <typename T> __device__ __forceinline__ void m3_mul_adj(M3<T> &c, const M3<T> &a, const M3<T> &b)
+{
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            // sum_k a_ik conj(b_jk)
+            T sr = a.re[i][0] * b.re[j][0] + a.im[i][0] * b.im[j][0];
+            T si = a.im[i][0] * b.re[j][0] - a.re[i][0] * b.im[j][0];
+#pragma unroll
+            for (int k = 1; k < 3; k++) {
+                sr += a.re[i][k] * b.re[j][k] + a.im[i][k] * b.im[j][k];
+                si += a.im[i][k] * b.re[j][k] - a.re[i][k] * b.im[j][k];
+            }
+            c.re[i][j] = sr;
+            c.im[i][j] = si;
+        }
+}
+
+// row 2 = conj(row 0 x row 1): the third row of an SU(3) matrix from its
+// first two (the 12-parameter reconstruction, Sec. 3.1)
+template <typename T> __device__ __forceinline__ void m3_rebuild_row2(M3<T> &u)
+{
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        const int c = (b + 1) % 3, d = (b + 2) % 3;
+        T xr = u.re[0][c] * u.re[1][d] - u.im[0][c] * u.im[1][d] - (u.re[0][d] * u.re[1][c] - u.im[0][d] * u.im[1][c]);
+        T xi = u.re[0][c] * u.im[1][d] + u.im[0][c] * u.re[1][d] - (u.re[0][d] * u.im[1][c] + u.im[0][d] * u.re[1][c]);
+        u.re[2][b] = xr;
+        u.im[2][b] = -xi;
+    }
+}
+
+// Gram-Schmidt on rows 0 and 1, then row 2 = conj(row0 x row1)
+template <typename T> __device__ __forceinline__ void m3_reunitarize(M3<T> &u)
+{
+    T n0 = T(0);
+#pragma unroll
+    for (int b = 0; b < 3; b++) n0 += u.re[0][b] * u.re[0][b] + u.im[0][b] * u.im[0][b];
+    n0 = T(1) / sqrt(n0);
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        u.re[0][b] *= n0;
+        u.im[0][b] *= n0;
+    }
+    // ip = sum_b conj(r0_b) r1_b
+    T ipr = T(0), ipi = T(0);
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        ipr += u.re[0][b] * u.re[1][b] + u.im[0][b] * u.im[1][b];
+        ipi += u.re[0][b] * u.im[1][b] - u.im[0][b] * u.re[1][b];
+    }
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        u.re[1][b] -= ipr * u.re[0][b] - ipi * u.im[0][b];
+        u.im[1][b] -= ipr * u.im[0][b] + ipi * u.re[0][b];
+    }
+    T n1 = T(0);
+#pragma unroll
+    for (int b = 0; b < 3; b++) n1 += u.re[1][b] * u.re[1][b] + u.im[1][b] * u.im[1][b];
+    n1 = T(1) / sqrt(n1);
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        u.re[1][b] *= n1;
+        u.im[1][b] *= n1;
+    }
+    m3_rebuild_row2(u);
+}
+
+// quaternion product (a0 + i a.s)(b0 + i b.s) = (a0 b0 - a.b) + i (a0 b + b0 a - a x b).s
+template <typename T> __device__ __forceinline__ Q4<T> q_mul(const Q4<T> &a, const Q4<T> &b)
+{
+    Q4<T> c;
+    c.a[0] = a.a[0] * b.a[0] - a.a[1] * b.a[1] - a.a[2] * b.a[2] - a.a[3] * b.a[3];
+    c.a[1] = a.a[0] * b.a[1] + b.a[0] * a.a[1] - (a.a[2] * b.a[3] - a.a[3] * b.a[2]);
+    c.a[2] = a.a[0] * b.a[2] + b.a[0] * a.a[2] - (a.a[3] * b.a[1] - a.a[1] * b.a[3]);
+    c.a[3] = a.a[0] * b.a[3] + b.a[0] * a.a[3] - (a.a[1] * b.a[2] - a.a[2] * b.a[1]);
+    return c;
+}
+
+// a b^+ (b^+ = (b0, -b))
+template <typename T> __device__ __forceinline__ Q4<T> q_mul_adj(const Q4<T> &a, const Q4<T> &b)
+{
+    Q4<T> bd = {{b.a[0], -b.a[1], -b.a[2], -b.a[3]}};
+    return q_mul(a, bd);
+}
+
+// ---------------------------------------------------------------------------
+// the local update of Sec. 2
+
+// The SU(2) element maximising Re tr[r w] for a block with quaternion part
+// proportional to (a0, a) is r = (a0, -a)/|a|; it is then replaced by r^omega.
+// variant 0: the binomial series 1 + omega (r-1) + omega(omega-1)/2 (r-1)^2,
+// which for a unit quaternion r = (c0, c) equals (1-omega) 1 + beta r with
+// beta = omega (1 + (omega-1)(c0-1)), rescaled to unit length.
+// variant 1: the exact power (cos(omega phi), c/|c| sin(omega phi)).
+// |a| = 0 leaves the block alone (q = 1).
+template <typename T>
+__device__ __forceinline__ void su2_or_step(T a0, T a1, T a2, T a3, T omega, int variant, T q[4])
+{
+    T n2 = a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3;
+    if (!(n2 > T(0))) {
+        q[0] = T(1);
+        q[1] = q[2] = q[3] = T(0);
+        return;
+    }
+    T inv = T(1) / sqrt(n2);
+    T c0 = a0 * inv, c1 = -a1 * inv, c2 = -a2 * inv, c3 = -a3 * inv;
+    if (variant == 0) {
+        T beta = omega * (T(1) + (omega - T(1)) * (c0 - T(1)));
+        T x0 = (T(1) - omega) + beta * c0;
+        T x1 = beta * c1, x2 = beta * c2, x3 = beta * c3;
+        T m = T(1) / sqrt(x0 * x0 + x1 * x1 + x2 * x2 + x3 * x3);
+        q[0] = x0 * m;
+        q[1] = x1 * m;
+        q[2] = x2 * m;
+        q[3] = x3 * m;
+    } else {
+        T s = sqrt(c1 * c1 + c2 * c2 + c3 * c3);
+        if (!(s > T(0))) {
+            q[0] = c0;
+            q[1] = c1;
+            q[2] = c2;
+            q[3] = c3;
+            return;
+        }
+        T phi = atan2(s, c0);
+        T f = sin(omega * phi) / s;
+        q[0] = cos(omega * phi);
+        q[1] = c1 * f;
+        q[2] = c2 * f;
+        q[3] = c3 * f;
+    }
+}
+
+// rows i, j of m  <-  R rows, R = [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]]
+template <typename T, int I, int J> __device__ __forceinline__ void rotate_rows(M3<T> &m, const T q[4])
+{
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        T xr = m.re[I][c], xi = m.im[I][c], yr = m.re[J][c], yi = m.im[J][c];
+        m.re[I][c] = q[0] * xr - q[3] * xi + q[2] * yr - q[1] * yi;
+        m.im[I][c] = q[0] * xi + q[3] * xr + q[2] * yi + q[1] * yr;
+        m.re[J][c] = -q[2] * xr - q[1] * xi + q[0] * yr + q[3] * yi;
+        m.im[J][c] = -q[2] * xi + q[1] * xr + q[0] * yi - q[3] * yr;
+    }
+}
+
+// quaternion part (times 2) of the (I,J) block of K
+template <typename T, int I, int J>
+__device__ __forceinline__ void block_quaternion(const M3<T> &K, T &a0, T &a1, T &a2, T &a3)
+{
+    a0 = K.re[I][I] + K.re[J][J];
+    a1 = K.im[I][J] + K.im[J][I];
+    a2 = K.re[I][J] - K.re[J][I];
+    a3 = K.im[I][I] - K.im[J][J];
+}
+
+// SU(3): subgroups (0,1), (0,2), (1,2) in that order, each maximising its
+// block of the running K (K <- R K) and overrelaxed; g = R12 R02 R01.
+// K is consumed.
+template <typename T> __device__ __forceinline__ void su3_local_gauge(M3<T> &K, M3<T> &g, T omega, int variant)
+{
+    T a0, a1, a2, a3, q[4];
+    block_quaternion<T, 0, 1>(K, a0, a1, a2, a3);
+    su2_or_step(a0, a1, a2, a3, omega, variant, q);
+    // g = R01
+    g.re[0][0] = q[0];  g.im[0][0] = q[3];
+    g.re[0][1] = q[2];  g.im[0][1] = q[1];
+    g.re[1][0] = -q[2]; g.im[1][0] = q[1];
+    g.re[1][1] = q[0];  g.im[1][1] = -q[3];
+    g.re[0][2] = g.im[0][2] = g.re[1][2] = g.im[1][2] = T(0);
+    g.re[2][0] = g.im[2][0] = g.re[2][1] = g.im[2][1] = T(0);
+    g.re[2][2] = T(1);
+    g.im[2][2] = T(0);
+    rotate_rows<T, 0, 1>(K, q);
+
+    block_quaternion<T, 0, 2>(K, a0, a1, a2, a3);
+    su2_or_step(a0, a1, a2, a3, omega, variant, q);
+    rotate_rows<T, 0, 2>(K, q);
+    rotate_rows<T, 0, 2>(g, q);
+
+    block_quaternion<T, 1, 2>(K, a0, a1, a2, a3);
+    su2_or_step(a0, a1, a2, a3, omega, variant, q);
+    rotate_rows<T, 1, 2>(g, q);
+}
+
+// SU(2): g = (K^+/sqrt(det K^+))^omega for the quaternion K = (k0, k):
+// the maximiser is (k0, -k)/|k|.
+template <typename T> __device__ __forceinline__ Q4<T> su2_local_gauge(const Q4<T> &K, T omega, int variant)
+{
+    Q4<T> g;
+    // su2_or_step takes the quaternion of the block and conjugates it itself
+    su2_or_step(K.a[0], K.a[1], K.a[2], K.a[3], omega, variant, g.a);
+    return g;
+}
+
+// ---------------------------------------------------------------------------
+// storage parameterisations (how a link sits in global memory)
+
+template <int NC, typename Real, int NREAL> struct Param;
+
+// SU(3), FP64, full 18 reals: 9 x double2, chunk k = element (k/3, k%3)
+template <> struct Param<3, double, 18> {
+    typedef double Real;
+    typedef double2 Chunk;
+    typedef M3<double> Link;
+    static constexpr int NC = 3, NREAL = 18, NCHUNK = 9;
+    static __device__ __forceinline__ void load(const Chunk *p, size_t s, Link &u)
+    {
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            double2 c = p[k * s];
+            u.re[k / 3][k % 3] = c.x;
+            u.im[k / 3][k % 3] = c.y;
+        }
+    }
+    static __device__ __forceinline__ void load_raw(const Chunk *p, size_t s, Link &u) { load(p, s, u); }
+    static __device__ __forceinline__ void store(Chunk *p, size_t s, const Link &u)
+    {
+#pragma unroll
+        for (int k = 0; k < 9; k++) p[k * s] = make_double2(u.re[k / 3][k % 3], u.im[k / 3][k % 3]);
+    }
+};
+
+// SU(3), FP64, first two rows (12 reals): 6 x double2, row 2 rebuilt on load
+template <> struct Param<3, double, 12> {
+    typedef double Real;
+    typedef double2 Chunk;
+    typedef M3<double> Link;
+    static constexpr int NC = 3, NREAL = 12, NCHUNK = 6;
+    static __device__ __forceinline__ void load_raw(const Chunk *p, size_t s, Link &u)
+    {
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            double2 c = p[k * s];
+            u.re[k / 3][k % 3] = c.x;
+            u.im[k / 3][k % 3] = c.y;
+        }
+    }
+    static __device__ __forceinline__ void load(const Chunk *p, size_t s, Link &u)
+    {
+        load_raw(p, s, u);
+        m3_rebuild_row2(u);
+    }
+    static __device__ __forceinline__ void store(Chunk *p, size_t s, const Link &u)
+    {
+#pragma unroll
+        for (int k = 0; k < 6; k++) p[k * s] = make_double2(u.re[k / 3][k % 3], u.im[k / 3][k % 3]);
+    }
+};
+
+// SU(3), FP32, first two rows: 3 x float4 = (U00,U01), (U02,U10), (U11,U12)
+// (Sec. 3.1's three-float4 parameterisation)
+template <> struct Param<3, float, 12> {
+    typedef float Real;
+    typedef float4 Chunk;
+    typedef M3<float> Link;
+    static constexpr int NC = 3, NREAL = 12, NCHUNK = 3;
+    static __device__ __forceinline__ void load_raw(const Chunk *p, size_t s, Link &u)
+    {
+        float4 c0 = p[0], c1 = p[s], c2 = p[2 * s];
+        u.re[0][0] = c0.x; u.im[0][0] = c0.y; u.re[0][1] = c0.z; u.im[0][1] = c0.w;
+        u.re[0][2] = c1.x; u.im[0][2] = c1.y; u.re[1][0] = c1.z; u.im[1][0] = c1.w;
+        u.re[1][1] = c2.x; u.im[1][1] = c2.y; u.re[1][2] = c2.z; u.im[1][2] = c2.w;
+    }
+    static __device__ __forceinline__ void load(const Chunk *p, size_t s, Link &u)
+    {
+        load_raw(p, s, u);
+        m3_rebuild_row2(u);
+    }
+    static __device__ __forceinline__ void store(Chunk *p, size_t s, const Link &u)
+    {
+        p[0] = make_float4(u.re[0][0], u.im[0][0], u.re[0][1], u.im[0][1]);
+        p[s] = make_float4(u.re[0][2], u.im[0][2], u.re[1][0], u.im[1][0]);
+        p[2 * s] = make_float4(u.re[1][1], u.im[1][1], u.re[1][2], u.im[1][2]);
+    }
+};
+
+// SU(3), FP32, full 18 reals: 9 x float2
+template <> struct Param<3, float, 18> {
+    typedef float Real;
+    typedef float2 Chunk;
+    typedef M3<float> Link;
+    static constexpr int NC = 3, NREAL = 18, NCHUNK = 9;
+    static __device__ __forceinline__ void load(const Chunk *p, size_t s, Link &u)
+    {
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            float2 c = p[k * s];
+            u.re[k / 3][k % 3] = c.x;
+            u.im[k / 3][k % 3] = c.y;
+        }
+    }
+    static __device__ __forceinline__ void load_raw(const Chunk *p, size_t s, Link &u) { load(p, s, u); }
+    static __device__ __forceinline__ void store(Chunk *p, size_t s, const Link &u)
+    {
+#pragma unroll
+        for (int k = 0; k < 9; k++) p[k * s] = make_float2(u.re[k / 3][k % 3], u.im[k / 3][k % 3]);
+    }
+};
+
+// SU(2), FP64 quaternion: 2 x double2 = (a0,a1), (a2,a3)
+template <> struct Param<2, double, 4> {
+    typedef double Real;
+    typedef double2 Chunk;
+    typedef Q4<double> Link;
+    static constexpr int NC = 2, NREAL = 4, NCHUNK = 2;
+    static __device__ __forceinline__ void load(const Chunk *p, size_t s, Link &u)
+    {
+        double2 c0 = p[0], c1 = p[s];
+        u.a[0] = c0.x; u.a[1] = c0.y; u.a[2] = c1.x; u.a[3] = c1.y;
+    }
+    static __device__ __forceinline__ void load_raw(const Chunk *p, size_t s, Link &u) { load(p, s, u); }
+    static __device__ __forceinline__ void store(Chunk *p, size_t s, const Link &u)
+    {
+        p[0] = make_double2(u.a[0], u.a[1]);
+        p[s] = make_double2(u.a[2], u.a[3]);
+    }
+};
+
+// SU(2), FP32 quaternion: 1 x float4
+template <> struct Param<2, float, 4> {
+    typedef float Real;
+    typedef float4 Chunk;
+    typedef Q4<float> Link;
+    static constexpr int NC = 2, NREAL = 4, NCHUNK = 1;
+    static __device__ __forceinline__ void load(const Chunk *p, size_t, Link &u)
+    {
+        float4 c = p[0];
+        u.a[0] = c.x; u.a[1] = c.y; u.a[2] = c.z; u.a[3] = c.w;
+    }
+    static __device__ __forceinline__ void load_raw(const Chunk *p, size_t s, Link &u) { load(p, s, u); }
+    static __device__ __forceinline__ void store(Chunk *p, size_t, const Link &u)
+    {
+        p[0] = make_float4(u.a[0], u.a[1], u.a[2], u.a[3]);
+    }
+};
+
+} // namespace culgt

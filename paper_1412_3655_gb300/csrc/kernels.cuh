@@ -1,0 +1,512 @@
+// Kernel templates of libculgt. Each .cu file of the library instantiates the
+// ones it needs; launch wrappers are declared in launch.h.
+#pragma once
+
+#include "culgt_device.cuh"
+
+namespace culgt {
+
+// ---------------------------------------------------------------------------
+// K2: one checkerboard half-sweep (Sec. 2): every site x of parity p gathers
+// K(x) = sum_mu [U_mu(x) + U_mu(x-mu)^+], builds g(x)^omega and applies it,
+// U_mu(x) <- g U_mu(x), U_mu(x-mu) <- U_mu(x-mu) g^+. One thread per site.
+// mu_first = 0 for Landau, 1 for Coulomb (spatial links only). Sites of one
+// parity share no link, so threads never touch the same link.
+//
+// KEEP = true holds the 8 links in registers between the gather and the
+// update (FP32 and SU(2): one read and one write of each link); KEEP = false
+// re-reads them from L1/L2 for the update (FP64 SU(3), whose 8 links would
+// need 288 registers).
+
+template <class P> struct KeepLinks {
+    static constexpr bool value = (sizeof(typename P::Real) * P::NREAL * 8 <= 4 * 12 * 8);
+};
+
+template <class P, bool KEEP>
+__device__ __forceinline__ void su3_site_update(typename P::Chunk *base, const Geom &g, int cb, int p, int mu_first,
+                                                typename P::Real omega, int variant, M3<typename P::Real> *gout)
+{
+    typedef typename P::Real T;
+    typedef typename P::Chunk C;
+    int x[4];
+    decode_site(g, cb, p, x);
+    const int q = p ^ 1;
+    C *fwd[4];
+    C *bwd[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        fwd[mu] = base + plane_offset(g, p, mu, P::NCHUNK) + cb;
+        bwd[mu] = base + plane_offset(g, q, mu, P::NCHUNK) + cb_shift(g, x, mu, -1);
+    }
+    M3<T> K;
+    m3_zero(K);
+    if (KEEP) {
+        M3<T> uf[4], ub[4];
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            if (mu < mu_first) continue;
+            P::load(fwd[mu], g.stride, uf[mu]);
+            P::load(bwd[mu], g.stride, ub[mu]);
+        }
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            if (mu < mu_first) continue;
+            m3_acc(K, uf[mu]);
+            m3_acc_adj(K, ub[mu]);
+        }
+        M3<T> G;
+        su3_local_gauge(K, G, omega, variant);
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            if (mu < mu_first) continue;
+            M3<T> t;
+            m3_mul(t, G, uf[mu]);
+            P::store(fwd[mu], g.stride, t);
+            m3_mul_adj(t, ub[mu], G);
+            P::store(bwd[mu], g.stride, t);
+        }
+        if (gout) *gout = G;
+    } else {
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            if (mu < mu_first) continue;
+            M3<T> u;
+            P::load(fwd[mu], g.stride, u);
+            m3_acc(K, u);
+            P::load(bwd[mu], g.stride, u);
+            m3_acc_adj(K, u);
+        }
+        M3<T> G;
+        su3_local_gauge(K, G, omega, variant);
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            if (mu < mu_first) continue;
+            M3<T> u, t;
+            P::load(fwd[mu], g.stride, u);
+            m3_mul(t, G, u);
+            P::store(fwd[mu], g.stride, t);
+            P::load(bwd[mu], g.stride, u);
+            m3_mul_adj(t, u, G);
+            P::store(bwd[mu], g.stride, t);
+        }
+        if (gout) *gout = G;
+    }
+}
+
+template <class P>
+__device__ __forceinline__ void su2_site_update(typename P::Chunk *base, const Geom &g, int cb, int p, int mu_first,
+                                                typename P::Real omega, int variant, Q4<typename P::Real> *gout)
+{
+    typedef typename P::Real T;
+    typedef typename P::Chunk C;
+    int x[4];
+    decode_site(g, cb, p, x);
+    const int q = p ^ 1;
+    C *fwd[4];
+    C *bwd[4];
+    Q4<T> uf[4], ub[4];
+    Q4<T> K = {{T(0), T(0), T(0), T(0)}};
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        fwd[mu] = base + plane_offset(g, p, mu, P::NCHUNK) + cb;
+        bwd[mu] = base + plane_offset(g, q, mu, P::NCHUNK) + cb_shift(g, x, mu, -1);
+        if (mu < mu_first) continue;
+        P::load(fwd[mu], g.stride, uf[mu]);
+        P::load(bwd[mu], g.stride, ub[mu]);
+    }
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        if (mu < mu_first) continue;
+        // U_f + U_b^+ : (f0 + b0, f - b)
+        K.a[0] += uf[mu].a[0] + ub[mu].a[0];
+        K.a[1] += uf[mu].a[1] - ub[mu].a[1];
+        K.a[2] += uf[mu].a[2] - ub[mu].a[2];
+        K.a[3] += uf[mu].a[3] - ub[mu].a[3];
+    }
+    Q4<T> G = su2_local_gauge(K, omega, variant);
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        if (mu < mu_first) continue;
+        P::store(fwd[mu], g.stride, q_mul(G, uf[mu]));
+        P::store(bwd[mu], g.stride, q_mul_adj(ub[mu], G));
+    }
+    if (gout) *gout = G;
+}
+
+template <class P>
+__global__ void __launch_bounds__(128) k_halfsweep(typename P::Chunk *base, Geom g, int parity, typename P::Real omega,
+                                                   int variant)
+{
+    int cb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cb >= g.Vh) return;
+    if constexpr (P::NC == 3)
+        su3_site_update<P, KeepLinks<P>::value>(base, g, cb, parity, 0, omega, variant, nullptr);
+    else
+        su2_site_update<P>(base, g, cb, parity, 0, omega, variant, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// K3: theta and F. Delta(x) is linear in the links, so with
+// M = sum_mu [U_mu(x) - U_mu(x-mu)],
+//   Delta = [(M - M^+)/(2i)]_traceless,
+//   tr[Delta Delta^+] = sum_a d_a^2 + 1/2 sum_{a<b} |M_ab - conj(M_ba)|^2,
+//   d_a = Im M_aa - (1/Nc) sum_b Im M_bb.
+// For SU(2) quaternions U = (u0, u): Delta = (sum_mu u_mu(x) - u_mu(x-mu)).s,
+// tr Delta^2 = 2 |.|^2, and Re tr U = 2 u0.
+// Per-site values are formed in the storage precision and accumulated in
+// FP64: warp shuffle, then the block, then one partial per block; a
+// single-block kernel sums the partials in a fixed order (deterministic).
+
+template <typename T>
+__device__ __forceinline__ void site_theta_su3(const M3<T> &M, double &th)
+{
+    T tr = M.im[0][0] + M.im[1][1] + M.im[2][2];
+    T d0 = M.im[0][0] - tr * T(1.0 / 3.0);
+    T d1 = M.im[1][1] - tr * T(1.0 / 3.0);
+    T d2 = M.im[2][2] - tr * T(1.0 / 3.0);
+    T s = d0 * d0 + d1 * d1 + d2 * d2;
+    T o = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = a + 1; b < 3; b++) {
+            T zr = M.re[a][b] - M.re[b][a];
+            T zi = M.im[a][b] + M.im[b][a];
+            o += zr * zr + zi * zi;
+        }
+    th = (double)s + 0.5 * (double)o;
+}
+
+__device__ __forceinline__ void block_reduce2(double a, double b, double2 *partials)
+{
+    __shared__ double sa[32], sb[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        sa[w] = a;
+        sb[w] = b;
+    }
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        a = lane < nw ? sa[lane] : 0.0;
+        b = lane < nw ? sb[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) partials[blockIdx.x] = make_double2(a, b);
+    }
+}
+
+// one thread per site of both parities: site index s in [0, 2 Vh), parity s / Vh
+template <class P>
+__global__ void __launch_bounds__(256) k_theta(const typename P::Chunk *base, Geom g, int mu_first, double2 *partials)
+{
+    typedef typename P::Real T;
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double th = 0.0, fs = 0.0;
+    if (s < 2 * g.Vh) {
+        int p = s >= g.Vh;
+        int cb = s - p * g.Vh;
+        int x[4];
+        decode_site(g, cb, p, x);
+        if constexpr (P::NC == 3) {
+            M3<T> M;
+            m3_zero(M);
+            T f = T(0);
+#pragma unroll
+            for (int mu = 0; mu < 4; mu++) {
+                if (mu < mu_first) continue;
+                M3<T> u;
+                P::load(base + plane_offset(g, p, mu, P::NCHUNK) + cb, g.stride, u);
+                f += u.re[0][0] + u.re[1][1] + u.re[2][2];
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+#pragma unroll
+                    for (int b = 0; b < 3; b++) {
+                        M.re[a][b] += u.re[a][b];
+                        M.im[a][b] += u.im[a][b];
+                    }
+                P::load(base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1), g.stride, u);
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+#pragma unroll
+                    for (int b = 0; b < 3; b++) {
+                        M.re[a][b] -= u.re[a][b];
+                        M.im[a][b] -= u.im[a][b];
+                    }
+            }
+            site_theta_su3(M, th);
+            fs = (double)f;
+        } else {
+            T v1 = T(0), v2 = T(0), v3 = T(0), f = T(0);
+#pragma unroll
+            for (int mu = 0; mu < 4; mu++) {
+                if (mu < mu_first) continue;
+                Q4<T> u;
+                P::load(base + plane_offset(g, p, mu, P::NCHUNK) + cb, g.stride, u);
+                f += u.a[0];
+                v1 += u.a[1];
+                v2 += u.a[2];
+                v3 += u.a[3];
+                P::load(base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1), g.stride, u);
+                v1 -= u.a[1];
+                v2 -= u.a[2];
+                v3 -= u.a[3];
+            }
+            th = 2.0 * ((double)v1 * v1 + (double)v2 * v2 + (double)v3 * v3);
+            fs = 2.0 * (double)f;
+        }
+    }
+    block_reduce2(th, fs, partials);
+}
+
+// sums n partials in a fixed order; out[0] = sum.x * sx, out[1] = sum.y * sy
+__global__ void k_finalize2(const double2 *partials, int n, double sx, double sy, double *out);
+// out[0] = max over partials of .x
+__global__ void k_finalize_max(const double2 *partials, int n, double *out);
+
+// ---------------------------------------------------------------------------
+// plaquette, in FP64 whatever the storage
+
+template <class P> __device__ __forceinline__ void load_m3d(const typename P::Chunk *p, size_t s, M3<double> &u)
+{
+    M3<typename P::Real> t;
+    P::load(p, s, t);
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            u.re[a][b] = (double)t.re[a][b];
+            u.im[a][b] = (double)t.im[a][b];
+        }
+}
+
+template <class P> __device__ __forceinline__ void load_q4d(const typename P::Chunk *p, size_t s, Q4<double> &u)
+{
+    Q4<typename P::Real> t;
+    P::load(p, s, t);
+#pragma unroll
+    for (int k = 0; k < 4; k++) u.a[k] = (double)t.a[k];
+}
+
+template <class P>
+__global__ void __launch_bounds__(128) k_plaquette(const typename P::Chunk *base, Geom g, double2 *partials)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    if (s < 2 * g.Vh) {
+        int p = s >= g.Vh;
+        int cb = s - p * g.Vh;
+        int x[4];
+        decode_site(g, cb, p, x);
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++)
+#pragma unroll
+            for (int nu = mu + 1; nu < 4; nu++) {
+                const typename P::Chunk *a = base + plane_offset(g, p, mu, P::NCHUNK) + cb;
+                const typename P::Chunk *b = base + plane_offset(g, p ^ 1, nu, P::NCHUNK) + cb_shift(g, x, mu, 1);
+                const typename P::Chunk *c = base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, nu, 1);
+                const typename P::Chunk *d = base + plane_offset(g, p, nu, P::NCHUNK) + cb;
+                if constexpr (P::NC == 3) {
+                    M3<double> A, B, C, D, t1, t2;
+                    load_m3d<P>(a, g.stride, A);
+                    load_m3d<P>(b, g.stride, B);
+                    load_m3d<P>(c, g.stride, C);
+                    load_m3d<P>(d, g.stride, D);
+                    m3_mul(t1, A, B);
+                    m3_mul_adj(t2, t1, C);
+                    m3_mul_adj(t1, t2, D);
+                    acc += t1.re[0][0] + t1.re[1][1] + t1.re[2][2];
+                } else {
+                    Q4<double> A, B, C, D;
+                    load_q4d<P>(a, g.stride, A);
+                    load_q4d<P>(b, g.stride, B);
+                    load_q4d<P>(c, g.stride, C);
+                    load_q4d<P>(d, g.stride, D);
+                    Q4<double> t = q_mul_adj(q_mul_adj(q_mul(A, B), C), D);
+                    acc += 2.0 * t.a[0];
+                }
+            }
+    }
+    block_reduce2(acc, 0.0, partials);
+}
+
+// ---------------------------------------------------------------------------
+// K4: reunitarisation, one thread per (parity, mu, site)
+
+template <class P> __global__ void __launch_bounds__(256) k_reunitarize(typename P::Chunk *base, Geom g)
+{
+    typedef typename P::Real T;
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 8LL * g.Vh) return;
+    int plane = (int)(t / g.Vh);
+    int cb = (int)(t - (long long)plane * g.Vh);
+    typename P::Chunk *ptr = base + (size_t)plane * P::NCHUNK * g.stride + cb;
+    typename P::Link u;
+    P::load_raw(ptr, g.stride, u);
+    if constexpr (P::NC == 3) {
+        m3_reunitarize(u);
+    } else {
+        T n = T(1) / sqrt(u.a[0] * u.a[0] + u.a[1] * u.a[1] + u.a[2] * u.a[2] + u.a[3] * u.a[3]);
+#pragma unroll
+        for (int k = 0; k < 4; k++) u.a[k] *= n;
+    }
+    P::store(ptr, g.stride, u);
+}
+
+// ---------------------------------------------------------------------------
+// unitarity check: per-block max over links of max_ab |(U U^+ - 1)_ab|, in FP64
+
+template <class P>
+__global__ void __launch_bounds__(256) k_unitarity(const typename P::Chunk *base, Geom g, double2 *partials)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double worst = 0.0;
+    if (t < 8LL * g.Vh) {
+        int plane = (int)(t / g.Vh);
+        int cb = (int)(t - (long long)plane * g.Vh);
+        const typename P::Chunk *ptr = base + (size_t)plane * P::NCHUNK * g.stride + cb;
+        if constexpr (P::NC == 3) {
+            M3<double> u, uu;
+            load_m3d<P>(ptr, g.stride, u);
+            m3_mul_adj(uu, u, u);
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) {
+                    double er = uu.re[a][b] - (a == b ? 1.0 : 0.0), ei = uu.im[a][b];
+                    worst = fmax(worst, sqrt(er * er + ei * ei));
+                }
+        } else {
+            Q4<double> u;
+            load_q4d<P>(ptr, g.stride, u);
+            worst = fabs(u.a[0] * u.a[0] + u.a[1] * u.a[1] + u.a[2] * u.a[2] + u.a[3] * u.a[3] - 1.0);
+        }
+    }
+    __shared__ double sm[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_down_sync(0xffffffffu, worst, o));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = worst;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) m = fmax(m, sm[k]);
+        partials[blockIdx.x] = make_double2(m, 0.0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K1: canonical [V][4][Nc][Nc]{re,im} <-> internal layout, one thread per link.
+// SU(2) canonical 2x2 matrices enter through their quaternion part.
+
+template <class P, typename In>
+__global__ void __launch_bounds__(256) k_to_internal(const In *canon, typename P::Chunk *base, Geom g)
+{
+    typedef typename P::Real T;
+    long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= 4LL * g.V) return;
+    int i = (int)(l >> 2), mu = (int)(l & 3);
+    const In *src = canon + l * (2 * P::NC * P::NC);
+    int x[4];
+    x[1] = i % g.L[1];
+    int r = i / g.L[1];
+    x[2] = r % g.L[2];
+    r /= g.L[2];
+    x[3] = r % g.L[3];
+    x[0] = r / g.L[3];
+    int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+    typename P::Chunk *dst = base + plane_offset(g, p, mu, P::NCHUNK) + (i >> 1);
+    typename P::Link u;
+    if constexpr (P::NC == 3) {
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            u.re[k / 3][k % 3] = (T)src[2 * k];
+            u.im[k / 3][k % 3] = (T)src[2 * k + 1];
+        }
+    } else {
+        // [[w00, w01], [w10, w11]] -> (Re(w00+w11), Im(w01+w10), Re(w01-w10), Im(w00-w11)) / 2
+        double w00r = src[0], w00i = src[1], w01r = src[2], w01i = src[3];
+        double w10r = src[4], w10i = src[5], w11r = src[6], w11i = src[7];
+        u.a[0] = (T)(0.5 * (w00r + w11r));
+        u.a[1] = (T)(0.5 * (w01i + w10i));
+        u.a[2] = (T)(0.5 * (w01r - w10r));
+        u.a[3] = (T)(0.5 * (w00i - w11i));
+    }
+    P::store(dst, g.stride, u);
+}
+
+template <class P, typename Out>
+__global__ void __launch_bounds__(256) k_to_canonical(const typename P::Chunk *base, Out *canon, Geom g)
+{
+    long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= 4LL * g.V) return;
+    int i = (int)(l >> 2), mu = (int)(l & 3);
+    Out *dst = canon + l * (2 * P::NC * P::NC);
+    int x[4];
+    x[1] = i % g.L[1];
+    int r = i / g.L[1];
+    x[2] = r % g.L[2];
+    r /= g.L[2];
+    x[3] = r % g.L[3];
+    x[0] = r / g.L[3];
+    int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+    const typename P::Chunk *src = base + plane_offset(g, p, mu, P::NCHUNK) + (i >> 1);
+    typename P::Link u;
+    P::load(src, g.stride, u);
+    if constexpr (P::NC == 3) {
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            dst[2 * k] = (Out)u.re[k / 3][k % 3];
+            dst[2 * k + 1] = (Out)u.im[k / 3][k % 3];
+        }
+    } else {
+        dst[0] = (Out)u.a[0]; dst[1] = (Out)u.a[3];
+        dst[2] = (Out)u.a[2]; dst[3] = (Out)u.a[1];
+        dst[4] = (Out)(-u.a[2]); dst[5] = (Out)u.a[1];
+        dst[6] = (Out)u.a[0]; dst[7] = (Out)(-u.a[3]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K5: precision switch FP32 -> FP64, one thread per (parity, mu, site): the
+// stored rows are widened and the link reunitarised in FP64 (row 2 rebuilt).
+
+template <class PIn, class POut>
+__global__ void __launch_bounds__(256) k_widen(const typename PIn::Chunk *src, typename POut::Chunk *dst, Geom g)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 8LL * g.Vh) return;
+    int plane = (int)(t / g.Vh);
+    int cb = (int)(t - (long long)plane * g.Vh);
+    typename PIn::Link a;
+    PIn::load_raw(src + (size_t)plane * PIn::NCHUNK * g.stride + cb, g.stride, a);
+    typename POut::Link b;
+    if constexpr (PIn::NC == 3) {
+#pragma unroll
+        for (int r = 0; r < 2; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                b.re[r][c] = (double)a.re[r][c];
+                b.im[r][c] = (double)a.im[r][c];
+            }
+        m3_reunitarize(b);
+    } else {
+        double n = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            b.a[k] = (double)a.a[k];
+            n += b.a[k] * b.a[k];
+        }
+        n = 1.0 / sqrt(n);
+#pragma unroll
+        for (int k = 0; k < 4; k++) b.a[k] *= n;
+    }
+    POut::store(dst + (size_t)plane * POut::NCHUNK * g.stride + cb, g.stride, b);
+}
+
+} // namespace culgt

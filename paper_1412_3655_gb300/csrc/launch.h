@@ -1,0 +1,53 @@
+// Host-side launch interface between the C ABI (api.cu) and the kernel
+// instantiations (ops_*.cu). One Ops table per storage parameterisation.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "culgt_device.cuh"
+
+namespace culgt {
+
+struct Ops {
+    int nc;         // 2 or 3
+    int nreal;      // reals per link in device memory
+    int fp32;       // 1 if the links are float
+    int nchunk;     // chunks per link
+    int chunk_bytes;
+    // one checkerboard half-sweep of the given parity (mu_first 0: Landau)
+    void (*halfsweep)(void *base, const Geom &g, int parity, double omega, int variant, cudaStream_t s);
+    // per-block partial sums of (tr Delta Delta^+, sum Re tr U) over all sites; returns the block count
+    int (*theta_partials)(const void *base, const Geom &g, int mu_first, double2 *partials, cudaStream_t s);
+    // per-block partial sums of the plaquette trace; returns the block count
+    int (*plaq_partials)(const void *base, const Geom &g, double2 *partials, cudaStream_t s);
+    void (*reunitarize)(void *base, const Geom &g, cudaStream_t s);
+    // per-block max of |U U^+ - 1| over all links; returns the block count
+    int (*unitarity_partials)(const void *base, const Geom &g, double2 *partials, cudaStream_t s);
+    void (*to_internal_d)(const double *canon, void *base, const Geom &g, cudaStream_t s);
+    void (*to_internal_f)(const float *canon, void *base, const Geom &g, cudaStream_t s);
+    void (*to_canonical_d)(const void *base, double *canon, const Geom &g, cudaStream_t s);
+    void (*to_canonical_f)(const void *base, float *canon, const Geom &g, cudaStream_t s);
+};
+
+// host-side count of kernel launches (culgt_kernel_launches)
+void count_launch(int n = 1);
+long long launches_so_far();
+
+// nullptr if the combination is not built
+const Ops *get_ops(int nc, int fp32, int nreal);
+
+// FP32 links (any storage) -> FP64 links (18 reals for SU(3)), reunitarised in FP64
+void launch_widen(const Ops *from, const void *src, const Ops *to, void *dst, const Geom &g, cudaStream_t s);
+
+// largest number of partials any reduction launch writes for this geometry
+int max_partials(const Geom &g);
+
+// out[0] = max_k partials[k].x
+void launch_finalize_max(const double2 *partials, int n, double *out, cudaStream_t s);
+
+// out[0] = sx * sum_k partials[k].x, out[1] = sy * sum_k partials[k].y, fixed order
+void launch_finalize2(const double2 *partials, int n, double sx, double sy, double *out, cudaStream_t s);
+
+extern const Ops ops_su3_d18, ops_su3_d12, ops_su3_f12, ops_su3_f18, ops_su2_d4, ops_su2_f4;
+
+} // namespace culgt

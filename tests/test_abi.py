@@ -1,0 +1,95 @@
+"""The C ABI without a GPU: the library loads, exports what include/culgt.h
+declares, and rejects bad arguments on the host before any device work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1412_3655_gb300 import culgt
+    return culgt
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(culgt_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    so = ctypes.CDLL(lib.LIBRARY_PATH)
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing
+
+
+def test_status_strings(lib):
+    for s in range(-7, 2):
+        assert lib.culgt_status_string(s).startswith("CULGT_")
+    assert "unknown" in lib.culgt_status_string(42)
+
+
+def test_defaults_validate(lib):
+    p = lib.culgt_default_params(3, (8, 4, 4, 6))
+    assert p.omega == 1.7 and p.theta_target == 1e-12 and p.switch_theta == 1e-8
+    assert lib.culgt_validate(p) == lib.OK
+
+
+@pytest.mark.parametrize("change,code", [
+    ({"dims": (4, 3, 4, 4)}, -2),
+    ({"dims": (0, 4, 4, 4)}, -2),
+    ({"dims": (1024, 1024, 1024, 2)}, -2),
+    ({"nc": 4}, -3),
+    ({"storage_reals": 12, "nc": 2}, -3),
+    ({"storage_reals": 10}, -3),
+    ({"omega": 2.0}, -1),
+    ({"omega": 0.9}, -1),
+    ({"omega": float("nan")}, -1),
+    ({"check_every": 0}, -1),
+    ({"max_sweeps": -1}, -1),
+    ({"precision": 3}, -1),
+    ({"precision": 2, "switch_theta": 0.0}, -1),
+    ({"theta_target": float("inf")}, -1),
+    ({"dtype_in": 2}, -1),
+    ({"or_variant": 2}, -1),
+])
+def test_validate_rejects(lib, change, code):
+    p = lib.Params.defaults(3, (4, 4, 4, 4))
+    for k, v in change.items():
+        setattr(p, k, v)
+    assert lib.culgt_validate(p) == code
+    # the one-call entry points check before touching the device
+    so = lib.library()
+    assert so.culgt_landau_fix(ctypes.c_void_p(16), ctypes.byref(p._c()), None, None) == code
+
+
+def test_null_pointers_rejected(lib):
+    p = lib.Params.defaults(3, (4, 4, 4, 4))
+    so = lib.library()
+    assert so.culgt_landau_fix(None, ctypes.byref(p._c()), None, None) == lib.ERR_ARG
+    assert so.culgt_landau_fix(ctypes.c_void_p(16), None, None, None) == lib.ERR_ARG
+    assert so.culgt_sweep(ctypes.c_void_p(16), ctypes.byref(p._c()), -1, None) == lib.ERR_ARG
+    assert so.culgt_create(ctypes.byref(p._c()), None, None) == lib.ERR_ARG
+
+
+def test_workspace_bytes(lib):
+    p = lib.Params.defaults(3, (32, 32, 32, 32))
+    # FP64, 18 reals: 4V links x 144 B plus reduction scratch
+    b = lib.culgt_workspace_bytes(p)
+    V = 32 ** 4
+    assert 4 * V * 144 <= b < 4 * V * 144 * 1.01
+    p.precision = lib.MIXED
+    b2 = lib.culgt_workspace_bytes(p)
+    assert b2 == pytest.approx(4 * V * (144 + 48), rel=0.01)

@@ -1,0 +1,265 @@
+"""CUDA path against the FP64 CPU oracle, through the C ABI.
+
+Tolerances (element by element on the canonical links):
+  FP64 storage, after one sweep: 1e-13
+  FP32 storage, after one sweep: 5e-6
+  converged F: 1e-10 relative;  plaquette unchanged: 1e-12.
+FP32 runs start from the FP32-rounded input on both sides, so only the
+arithmetic of one sweep is compared. FP32 theta is formed per site in FP32
+and accumulated in FP64; its tolerance, 1e-6 relative plus 1e-5 absolute,
+follows from per-element rounding of 6e-8 on sums of 16 links.
+"""
+import numpy as np
+import pytest
+
+from paper_1412_3655_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1412_3655_gb300 import culgt
+    return culgt
+
+
+def to_dev(U, dtype=np.float64):
+    real = np.ascontiguousarray(U).view(np.float64).astype(dtype)
+    return torch.from_numpy(real).cuda()
+
+
+def from_dev(t, shape):
+    a = t.cpu().numpy().astype(np.float64)
+    return np.ascontiguousarray(a).view(np.complex128).reshape(shape)
+
+
+def round32(U):
+    return U.view(np.float64).astype(np.float32).astype(np.float64).view(np.complex128)
+
+
+CASES = [
+    # dims, nc: several 128-site tiles with a ragged tail, L1 = 2, non-cubic, tiny
+    ((8, 8, 8, 8), 3),
+    ((6, 4, 6, 10), 3),
+    ((4, 2, 6, 4), 3),
+    ((2, 2, 2, 2), 3),
+    ((8, 8, 8, 8), 2),
+    ((6, 4, 6, 10), 2),
+    ((2, 2, 2, 2), 2),
+]
+
+
+@pytest.mark.parametrize("dims,nc", CASES)
+@pytest.mark.parametrize("omega,variant", [(1.7, 0), (1.0, 0), (1.75, 1)])
+def test_one_sweep_fp64(cu, orc, dims, nc, omega, variant):
+    U = synth.gauge_config(dims, nc, 0.3, 2)
+    storages = [18, 12] if nc == 3 else [4]
+    for sr in storages:
+        d = to_dev(U)
+        p = cu.Params.defaults(nc, dims, omega=omega, or_variant=variant, storage_reals=sr)
+        cu.culgt_sweep(d, p, 1)
+        ref = U.copy()
+        orc.sweep(ref, dims, nc, omega, 1, variant)
+        got = from_dev(d, U.shape)
+        assert np.abs(got - ref).max() <= 1e-13, f"storage {sr}"
+
+
+@pytest.mark.parametrize("dims,nc", CASES)
+def test_one_sweep_fp32(cu, orc, dims, nc):
+    U = round32(synth.gauge_config(dims, nc, 0.3, 3))
+    storages = [12, 18] if nc == 3 else [4]
+    for sr in storages:
+        d = to_dev(U)
+        p = cu.Params.defaults(nc, dims, precision=cu.FP32, storage_reals=sr)
+        cu.culgt_sweep(d, p, 1)
+        ref = U.copy()
+        orc.sweep(ref, dims, nc, 1.7, 1)
+        got = from_dev(d, U.shape)
+        assert np.abs(got - ref).max() <= 5e-6, f"storage {sr}"
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_float_canonical_buffer(cu, orc, nc):
+    dims = (4, 4, 4, 4)
+    U = round32(synth.gauge_config(dims, nc, 0.3, 4))
+    d = to_dev(U, np.float32)
+    p = cu.Params.defaults(nc, dims, precision=cu.FP32, dtype_in=1)
+    cu.culgt_sweep(d, p, 1)
+    ref = U.copy()
+    orc.sweep(ref, dims, nc, 1.7, 1)
+    assert np.abs(from_dev(d, U.shape) - ref).max() <= 5e-6
+
+
+@pytest.mark.parametrize("dims,nc", CASES)
+def test_theta_F_plaquette(cu, orc, dims, nc):
+    U = synth.gauge_config(dims, nc, 0.3, 5)
+    d = to_dev(U)
+    p = cu.Params.defaults(nc, dims)
+    th, F = cu.culgt_theta(d, p)
+    th_ref, F_ref = orc.theta(U, dims, nc)
+    assert th == pytest.approx(th_ref, rel=1e-12)
+    assert F == pytest.approx(F_ref, rel=1e-12, abs=1e-14)
+    assert cu.culgt_plaquette(d, p) == pytest.approx(orc.plaquette(U, dims, nc), rel=1e-12)
+    U32 = round32(U)
+    p32 = cu.Params.defaults(nc, dims, precision=cu.FP32)
+    th32, F32 = cu.culgt_theta(to_dev(U32), p32)
+    th_ref32, F_ref32 = orc.theta(U32, dims, nc)
+    assert th32 == pytest.approx(th_ref32, rel=1e-6, abs=1e-5)
+    assert F32 == pytest.approx(F_ref32, rel=1e-6)
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_theta_near_convergence(cu, orc, nc):
+    """Small theta (a converged field) is resolved in FP64."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_config(dims, nc, 0.3, 1)
+    orc.landau_fix(U, dims, nc, 1.7, 1e-14, 3000, 1)
+    th_ref, F_ref = orc.theta(U, dims, nc)
+    th, F = cu.culgt_theta(to_dev(U), cu.Params.defaults(nc, dims))
+    assert th == pytest.approx(th_ref, rel=1e-6, abs=1e-22)
+    assert F == pytest.approx(F_ref, rel=1e-13)
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_reunitarize(cu, orc, nc):
+    dims = (4, 4, 2, 6)
+    U = synth.gauge_config(dims, nc, 0.3, 6)
+    noisy = U + 1e-7 * np.random.default_rng(1).standard_normal(U.shape)
+    if nc == 2:  # SU(2) links enter through their quaternion part: keep the noise in it
+        noisy = U * (1 + 1e-7 * np.random.default_rng(1).standard_normal(U.shape[:2] + (1, 1)))
+    d = to_dev(np.ascontiguousarray(noisy))
+    cu.culgt_reunitarize(d, cu.Params.defaults(nc, dims))
+    ref = np.ascontiguousarray(noisy).copy()
+    orc.reunitarize(ref, nc)
+    assert np.abs(from_dev(d, U.shape) - ref).max() <= 1e-14
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_sweeps_keep_plaquette_and_unitarity(cu, orc, nc):
+    dims = (8, 8, 8, 8)
+    U = synth.gauge_config(dims, nc, 0.3, 7)
+    d = to_dev(U)
+    p = cu.Params.defaults(nc, dims)
+    P0 = cu.culgt_plaquette(d, p)
+    cu.culgt_sweep(d, p, 20)
+    assert cu.culgt_plaquette(d, p) == pytest.approx(P0, abs=1e-12)
+    assert orc.unitarity_error(from_dev(d, U.shape), nc) < 1e-13
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+@pytest.mark.parametrize("check_every", [1, 7])
+def test_landau_fix_fp64_matches_oracle(cu, orc, nc, check_every):
+    """4^4, eps = 0.3, seed 1, omega = 1.7, theta < 1e-12: same sweep count,
+    F within 1e-10 relative, plaquette unchanged to 1e-12."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_config(dims, nc, 0.3, 1)
+    d = to_dev(U)
+    p = cu.Params.defaults(nc, dims, check_every=check_every, reunit_every=50, max_sweeps=2000)
+    r = cu.culgt_landau_fix(d, p)
+    ref = U.copy()
+    rr = orc.landau_fix(ref, dims, nc, 1.7, 1e-12, 2000, check_every, 50)
+    assert r.status == cu.OK and rr["converged"]
+    assert r.sweeps_fp64 == rr["sweeps"]
+    assert r.F == pytest.approx(rr["F"], rel=1e-10)
+    assert r.theta < 1e-12
+    assert r.plaq_after == pytest.approx(r.plaq_before, abs=1e-12)
+    assert r.unitarity_err < 1e-13
+    assert np.abs(from_dev(d, U.shape) - ref).max() < 1e-9
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_landau_fix_mixed(cu, orc, nc):
+    """FP32 to theta < 1e-8, then FP64 to 1e-12: same local maximum as the
+    FP64 oracle here, F within 1e-10 relative."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_config(dims, nc, 0.3, 1)
+    d = to_dev(U)
+    p = cu.Params.defaults(nc, dims, precision=cu.MIXED, check_every=5, reunit_every=50, max_sweeps=3000)
+    r = cu.culgt_landau_fix(d, p)
+    ref = U.copy()
+    rr = orc.landau_fix(ref, dims, nc, 1.7, 1e-12, 3000, 1)
+    assert r.status == cu.OK
+    assert r.sweeps_fp32 > 0 and r.sweeps_fp64 > 0
+    assert r.theta < 1e-12
+    assert r.F == pytest.approx(rr["F"], rel=1e-10)
+    assert r.plaq_after == pytest.approx(r.plaq_before, abs=1e-12)
+    th, F = orc.theta(from_dev(d, U.shape), dims, nc)
+    assert th < 1e-12 and F == pytest.approx(r.F, rel=1e-12)
+
+
+def test_not_converged_status(cu):
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_config(dims, 3, 0.3, 1)
+    p = cu.Params.defaults(3, dims, max_sweeps=3, check_every=2)
+    r = cu.culgt_landau_fix(to_dev(U), p)
+    assert r.status == cu.NOT_CONVERGED and r.sweeps_fp64 == 3
+
+
+def test_nonfinite_input_is_reported(cu):
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_config(dims, 3, 0.3, 1)
+    U[17, 2, 1, 1] = np.nan
+    with pytest.raises(cu.CulgtError) as e:
+        cu.culgt_landau_fix(to_dev(U), cu.Params.defaults(3, dims))
+    assert e.value.status == cu.ERR_NONFINITE
+
+
+def test_host_entry_point_matches_device(cu):
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_config(dims, 3, 0.3, 1)
+    p = cu.Params.defaults(3, dims, check_every=5)
+    d = to_dev(U)
+    r1 = cu.culgt_landau_fix(d, p)
+    h = torch.from_numpy(U.view(np.float64).copy())
+    r2 = cu.culgt_landau_fix_host(h, p)
+    assert r1.sweeps_fp64 == r2.sweeps_fp64 and r1.F == r2.F
+    assert torch.equal(h, d.cpu())
+
+
+def test_handle_api_sequence(cu, orc):
+    dims = (6, 4, 6, 10)
+    U = synth.gauge_config(dims, 3, 0.3, 8)
+    d = to_dev(U)
+    p = cu.Params.defaults(3, dims, precision=cu.MIXED)
+    with cu.Handle(p) as h:
+        h.culgt_load(d)
+        h.culgt_handle_sweep(2)
+        h.culgt_handle_to_fp64()
+        h.culgt_handle_sweep(1)
+        th, F = h.culgt_handle_theta()
+        out = torch.empty_like(d)
+        h.culgt_store(out)
+        torch.cuda.synchronize()
+    ref = round32(U)
+    orc.sweep(ref, dims, 3, 1.7, 2)
+    orc.sweep(ref, dims, 3, 1.7, 1)
+    got = from_dev(out, U.shape)
+    assert np.abs(got - ref).max() < 1e-5
+    th_ref, F_ref = orc.theta(got, dims, 3)
+    assert th == pytest.approx(th_ref, rel=1e-12) and F == pytest.approx(F_ref, rel=1e-13)
+
+
+@pytest.mark.parametrize("nc", [3, 2])
+def test_full_size_32_one_sweep(cu, orc, nc):
+    """32^4 (the throughput workload): one sweep in FP64 and in FP32-12
+    against the oracle on the whole lattice."""
+    dims = (32, 32, 32, 32)
+    U = synth.gauge_config(dims, nc, 0.3, 2)
+    ref = U.copy()
+    orc.sweep(ref, dims, nc, 1.7, 1)
+    d = to_dev(U)
+    cu.culgt_sweep(d, cu.Params.defaults(nc, dims), 1)
+    assert np.abs(from_dev(d, U.shape) - ref).max() <= 1e-13
+    del d
+    U32 = round32(U)
+    ref = U32.copy()
+    orc.sweep(ref, dims, nc, 1.7, 1)
+    d = to_dev(U32)
+    cu.culgt_sweep(d, cu.Params.defaults(nc, dims, precision=cu.FP32), 1)
+    assert np.abs(from_dev(d, U.shape) - ref).max() <= 5e-6
