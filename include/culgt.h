@@ -126,7 +126,11 @@ culgt_status culgt_handle_sweep(culgt_handle *h, int n_sweeps);
 culgt_status culgt_handle_theta(culgt_handle *h, double *theta, double *F);
 culgt_status culgt_handle_plaquette(culgt_handle *h, double *plaq);
 culgt_status culgt_handle_reunitarize(culgt_handle *h);
-/* Converts FP32 links to FP64 (third row rebuilt, FP64 reunitarisation). */
+/* Switches a mixed handle to FP64. The FP32 phase keeps, per site, the
+ * product g(x) of its own updates; the switch reunitarises g in FP64 and
+ * sets U_mu(x) = g(x) U0_mu(x) g(x+mu)^+ from the FP64 input U0 loaded by
+ * culgt_load, so FP32 rounding never moves the links off the gauge orbit of
+ * the input (the plaquette is kept to FP64 rounding). No-op in FP64. */
 culgt_status culgt_handle_to_fp64(culgt_handle *h);
 /* Iterates to theta_target as the precision field says (mixed: FP32 until
  * theta < switch_theta, then FP64). Leaves the result in the handle. */

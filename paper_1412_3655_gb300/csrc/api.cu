@@ -26,6 +26,7 @@ struct culgt_handle {
     double *d_scalars;  // 4 doubles
     double *h_scalars;  // pinned, 4 doubles
     void *staging;      // canonical device buffer for the host entry point
+    void *gacc;         // mixed: FP32 accumulated gauge transformation per site
     int sweeps32, sweeps64;
 };
 
@@ -96,6 +97,11 @@ void pick_ops(const culgt_params *p, const Ops **o32, const Ops **o64)
     }
 }
 
+size_t gauge_bytes(const Ops *o32, const Geom &g)
+{
+    return (size_t)2 * o32->gauge_nchunk * g.stride * o32->gauge_chunk_bytes;
+}
+
 size_t canonical_bytes(const culgt_params *p, const Geom &g)
 {
     return (size_t)g.V * 4 * p->nc * p->nc * 2 * (p->dtype_in ? sizeof(float) : sizeof(double));
@@ -144,14 +150,25 @@ culgt_status unitarity_now(culgt_handle *h, double *err)
     return CULGT_OK;
 }
 
+// In the FP32 phase of a mixed handle the half-sweeps also accumulate g(x).
 void sweep_now(culgt_handle *h, int n)
 {
     const Ops *o = cur_ops(h);
     void *b = cur_buf(h);
-    for (int k = 0; k < n; k++) {
-        o->halfsweep(b, h->geom, 0, h->prm.omega, h->prm.or_variant, h->stream);
-        o->halfsweep(b, h->geom, 1, h->prm.omega, h->prm.or_variant, h->stream);
-    }
+    const bool acc = h->cur32 && h->gacc;
+    for (int k = 0; k < n; k++)
+        for (int parity = 0; parity < 2; parity++) {
+            if (acc)
+                o->halfsweep_acc(b, h->gacc, h->geom, parity, h->prm.omega, h->prm.or_variant, h->stream);
+            else
+                o->halfsweep(b, h->geom, parity, h->prm.omega, h->prm.or_variant, h->stream);
+        }
+}
+
+void reunitarize_now(culgt_handle *h)
+{
+    cur_ops(h)->reunitarize(cur_buf(h), h->geom, h->stream);
+    if (h->cur32 && h->gacc) h->ops32->gauge_reunitarize(h->gacc, h->geom, h->stream);
 }
 
 // Sweeps the current links until theta < target or the running total n
@@ -167,7 +184,7 @@ culgt_status run_phase(culgt_handle *h, double target, int *n, int *phase_sweeps
             sweep_now(h, 1);
             ++*n;
             ++*phase_sweeps;
-            if (p.reunit_every > 0 && *n % p.reunit_every == 0) cur_ops(h)->reunitarize(cur_buf(h), h->geom, h->stream);
+            if (p.reunit_every > 0 && *n % p.reunit_every == 0) reunitarize_now(h);
         }
         ST(theta_now(h, theta, F));
     }
@@ -276,6 +293,7 @@ culgt_status culgt_workspace_bytes(const culgt_params *p, size_t *bytes)
     size_t b = (size_t)max_partials(g) * sizeof(double2) + 4 * sizeof(double);
     if (o32) b += buffer_bytes(o32, g);
     if (o64) b += buffer_bytes(o64, g);
+    if (o32 && o64) b += gauge_bytes(o32, g);
     *bytes = b;
     return CULGT_OK;
 }
@@ -296,6 +314,8 @@ culgt_status culgt_create(const culgt_params *p, void *cuda_stream, culgt_handle
     culgt_status st = CULGT_OK;
     if (h->ops32 && cudaMalloc(&h->buf32, buffer_bytes(h->ops32, h->geom)) != cudaSuccess) st = CULGT_ERR_OOM;
     if (st == CULGT_OK && h->ops64 && cudaMalloc(&h->buf64, buffer_bytes(h->ops64, h->geom)) != cudaSuccess)
+        st = CULGT_ERR_OOM;
+    if (st == CULGT_OK && h->ops32 && h->ops64 && cudaMalloc(&h->gacc, gauge_bytes(h->ops32, h->geom)) != cudaSuccess)
         st = CULGT_ERR_OOM;
     if (st == CULGT_OK &&
         cudaMalloc((void **)&h->partials, (size_t)max_partials(h->geom) * sizeof(double2)) != cudaSuccess)
@@ -321,18 +341,26 @@ void culgt_destroy(culgt_handle *h)
     if (h->d_scalars) cudaFree(h->d_scalars);
     if (h->h_scalars) cudaFreeHost(h->h_scalars);
     if (h->staging) cudaFree(h->staging);
+    if (h->gacc) cudaFree(h->gacc);
     delete h;
 }
 
+// A mixed handle loads both precisions: the FP32 links it sweeps first and
+// the FP64 links the switch rotates by the accumulated g (orbit-exact).
 culgt_status culgt_load(culgt_handle *h, const void *d_links)
 {
     if (!h || !d_links) return CULGT_ERR_ARG;
+    const Ops *os[2] = {h->ops32, h->ops64};
+    void *bs[2] = {h->buf32, h->buf64};
+    for (int k = 0; k < 2; k++) {
+        if (!os[k]) continue;
+        if (h->prm.dtype_in)
+            os[k]->to_internal_f((const float *)d_links, bs[k], h->geom, h->stream);
+        else
+            os[k]->to_internal_d((const double *)d_links, bs[k], h->geom, h->stream);
+    }
+    if (h->gacc) h->ops32->gauge_identity(h->gacc, h->geom, h->stream);
     h->cur32 = h->ops32 != nullptr;
-    const Ops *o = cur_ops(h);
-    if (h->prm.dtype_in)
-        o->to_internal_f((const float *)d_links, cur_buf(h), h->geom, h->stream);
-    else
-        o->to_internal_d((const double *)d_links, cur_buf(h), h->geom, h->stream);
     CU(cudaGetLastError());
     h->loaded = 1;
     return CULGT_OK;
@@ -377,7 +405,7 @@ culgt_status culgt_handle_plaquette(culgt_handle *h, double *plaq)
 culgt_status culgt_handle_reunitarize(culgt_handle *h)
 {
     if (!h || !h->loaded) return CULGT_ERR_ARG;
-    cur_ops(h)->reunitarize(cur_buf(h), h->geom, h->stream);
+    reunitarize_now(h);
     CU(cudaGetLastError());
     return CULGT_OK;
 }
@@ -387,7 +415,10 @@ culgt_status culgt_handle_to_fp64(culgt_handle *h)
     if (!h || !h->loaded) return CULGT_ERR_ARG;
     if (!h->cur32) return CULGT_OK;
     if (!h->ops64) return CULGT_ERR_ARG;  // an FP32-only handle has no FP64 buffer
-    launch_widen(h->ops32, h->buf32, h->ops64, h->buf64, h->geom, h->stream);
+    if (h->gacc)
+        launch_rotate_orbit(h->ops32, h->gacc, h->ops64, h->buf64, h->geom, h->stream);
+    else
+        launch_widen(h->ops32, h->buf32, h->ops64, h->buf64, h->geom, h->stream);
     CU(cudaGetLastError());
     h->cur32 = 0;
     return CULGT_OK;

@@ -341,11 +341,14 @@ __global__ void __launch_bounds__(128) k_plaquette(const typename P::Chunk *base
 // ---------------------------------------------------------------------------
 // K4: reunitarisation, one thread per (parity, mu, site)
 
-template <class P> __global__ void __launch_bounds__(256) k_reunitarize(typename P::Chunk *base, Geom g)
+// over nplanes planes of links: 8 for the links (parity x mu), 2 for a
+// per-site gauge transformation (parity)
+template <class P>
+__global__ void __launch_bounds__(256) k_reunitarize(typename P::Chunk *base, Geom g, int nplanes)
 {
     typedef typename P::Real T;
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 8LL * g.Vh) return;
+    if (t >= (long long)nplanes * g.Vh) return;
     int plane = (int)(t / g.Vh);
     int cb = (int)(t - (long long)plane * g.Vh);
     typename P::Chunk *ptr = base + (size_t)plane * P::NCHUNK * g.stride + cb;
@@ -507,6 +510,112 @@ __global__ void __launch_bounds__(256) k_widen(const typename PIn::Chunk *src, t
         for (int k = 0; k < 4; k++) b.a[k] *= n;
     }
     POut::store(dst + (size_t)plane * POut::NCHUNK * g.stride + cb, g.stride, b);
+}
+
+// ---------------------------------------------------------------------------
+// Orbit-exact mixed precision. During the FP32 phase each site also keeps
+// the product of its own updates, gacc(x) <- g(x) gacc(x) (FP32, two rows for
+// SU(3), a quaternion for SU(2)), in planes [parity][chunk][cb]. At the
+// switch the FP64 links are rebuilt from the untouched FP64 input,
+// U_mu(x) <- g(x) U_mu(x) g(x+mu)^+ with g reunitarised in FP64, so the FP32
+// rounding of the links never leaves the gauge orbit of the input.
+
+template <class PG> __device__ __forceinline__ typename PG::Chunk *gauge_ptr(typename PG::Chunk *gb, const Geom &g,
+                                                                             int p, int cb)
+{
+    return gb + (size_t)p * PG::NCHUNK * g.stride + cb;
+}
+
+template <class P, class PG>
+__global__ void __launch_bounds__(128) k_halfsweep_acc(typename P::Chunk *base, typename PG::Chunk *gbase, Geom g,
+                                                       int parity, typename P::Real omega, int variant)
+{
+    typedef typename P::Real T;
+    int cb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cb >= g.Vh) return;
+    typename PG::Chunk *gp = gauge_ptr<PG>(gbase, g, parity, cb);
+    if constexpr (P::NC == 3) {
+        M3<T> G, A, B;
+        su3_site_update<P, KeepLinks<P>::value>(base, g, cb, parity, 0, omega, variant, &G);
+        PG::load(gp, g.stride, A);
+        m3_mul(B, G, A);
+        PG::store(gp, g.stride, B);
+    } else {
+        Q4<T> G, A;
+        su2_site_update<P>(base, g, cb, parity, 0, omega, variant, &G);
+        PG::load(gp, g.stride, A);
+        PG::store(gp, g.stride, q_mul(G, A));
+    }
+}
+
+template <class PG> __global__ void __launch_bounds__(256) k_gauge_identity(typename PG::Chunk *gbase, Geom g)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2LL * g.Vh) return;
+    int p = (int)(t / g.Vh);
+    int cb = (int)(t - (long long)p * g.Vh);
+    typename PG::Link u;
+    if constexpr (PG::NC == 3)
+        m3_identity(u);
+    else
+        u.a[0] = 1, u.a[1] = u.a[2] = u.a[3] = 0;
+    PG::store(gauge_ptr<PG>(gbase, g, p, cb), g.stride, u);
+}
+
+// g(x) in FP64, reunitarised, from the FP32 accumulator
+template <class PG, typename L>
+__device__ __forceinline__ void gauge_fp64(const typename PG::Chunk *p, size_t s, L &out)
+{
+    typename PG::Link a;
+    PG::load_raw(p, s, a);
+    if constexpr (PG::NC == 3) {
+#pragma unroll
+        for (int r = 0; r < 2; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                out.re[r][c] = (double)a.re[r][c];
+                out.im[r][c] = (double)a.im[r][c];
+            }
+        m3_reunitarize(out);
+    } else {
+        double n = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            out.a[k] = (double)a.a[k];
+            n += out.a[k] * out.a[k];
+        }
+        n = 1.0 / sqrt(n);
+#pragma unroll
+        for (int k = 0; k < 4; k++) out.a[k] *= n;
+    }
+}
+
+// U_mu(x) <- g(x) U_mu(x) g(x+mu)^+ on the FP64 links, one thread per link
+template <class PG, class P64>
+__global__ void __launch_bounds__(128) k_rotate_orbit(const typename PG::Chunk *gbase, typename P64::Chunk *base,
+                                                      Geom g)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 8LL * g.Vh) return;
+    int plane = (int)(t / g.Vh);
+    int cb = (int)(t - (long long)plane * g.Vh);
+    int p = plane >> 2, mu = plane & 3;
+    int x[4];
+    decode_site(g, cb, p, x);
+    int cbf = cb_shift(g, x, mu, 1);
+    typename P64::Chunk *up = base + plane_offset(g, p, mu, P64::NCHUNK) + cb;
+    typename P64::Link u, gx, gf;
+    P64::load(up, g.stride, u);
+    gauge_fp64<PG>(gbase + (size_t)p * PG::NCHUNK * g.stride + cb, g.stride, gx);
+    gauge_fp64<PG>(gbase + (size_t)(p ^ 1) * PG::NCHUNK * g.stride + cbf, g.stride, gf);
+    if constexpr (P64::NC == 3) {
+        M3<double> t1, t2;
+        m3_mul(t1, gx, u);
+        m3_mul_adj(t2, t1, gf);
+        P64::store(up, g.stride, t2);
+    } else {
+        P64::store(up, g.stride, q_mul_adj(q_mul(gx, u), gf));
+    }
 }
 
 } // namespace culgt

@@ -21,6 +21,13 @@ struct Ops {
     // per-block partial sums of the plaquette trace; returns the block count
     int (*plaq_partials)(const void *base, const Geom &g, double2 *partials, cudaStream_t s);
     void (*reunitarize)(void *base, const Geom &g, cudaStream_t s);
+    // half-sweep that also accumulates gacc(x) <- g(x) gacc(x) (FP32 storage only)
+    void (*halfsweep_acc)(void *base, void *gacc, const Geom &g, int parity, double omega, int variant,
+                          cudaStream_t s);
+    void (*gauge_identity)(void *gacc, const Geom &g, cudaStream_t s);
+    void (*gauge_reunitarize)(void *gacc, const Geom &g, cudaStream_t s);
+    int gauge_nchunk;     // chunks per site of the FP32 accumulator (0 for FP64 storage)
+    int gauge_chunk_bytes;
     // per-block max of |U U^+ - 1| over all links; returns the block count
     int (*unitarity_partials)(const void *base, const Geom &g, double2 *partials, cudaStream_t s);
     void (*to_internal_d)(const double *canon, void *base, const Geom &g, cudaStream_t s);
@@ -38,6 +45,10 @@ const Ops *get_ops(int nc, int fp32, int nreal);
 
 // FP32 links (any storage) -> FP64 links (18 reals for SU(3)), reunitarised in FP64
 void launch_widen(const Ops *from, const void *src, const Ops *to, void *dst, const Geom &g, cudaStream_t s);
+
+// FP64 links <- g(x) U g(x+mu)^+ with g from the FP32 accumulator of `from`
+void launch_rotate_orbit(const Ops *from, const void *gacc, const Ops *to, void *base64, const Geom &g,
+                         cudaStream_t s);
 
 // largest number of partials any reduction launch writes for this geometry
 int max_partials(const Geom &g);

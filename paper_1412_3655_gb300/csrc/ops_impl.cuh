@@ -8,6 +8,11 @@ namespace culgt {
 
 static inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
+// accumulator parameterisation of the orbit-exact mixed schedule
+template <class P> struct GaugeParam {
+    typedef Param<P::NC, float, P::NC == 3 ? 12 : 4> type;
+};
+
 template <class P> struct OpsImpl {
     typedef typename P::Chunk C;
     static constexpr int kSweepThreads = 128;
@@ -36,7 +41,28 @@ template <class P> struct OpsImpl {
     }
     static void reunitarize(void *base, const Geom &g, cudaStream_t s)
     {
-        k_reunitarize<P><<<blocks_for(8LL * g.Vh, 256), 256, 0, s>>>((C *)base, g);
+        k_reunitarize<P><<<blocks_for(8LL * g.Vh, 256), 256, 0, s>>>((C *)base, g, 8);
+        count_launch();
+    }
+    typedef typename GaugeParam<P>::type PG;
+    static constexpr bool kFP32 = sizeof(typename P::Real) == 4;
+    static void halfsweep_acc(void *base, void *gacc, const Geom &g, int parity, double omega, int variant,
+                              cudaStream_t s)
+    {
+        if constexpr (kFP32) {
+            k_halfsweep_acc<P, PG><<<blocks_for(g.Vh, kSweepThreads), kSweepThreads, 0, s>>>(
+                (C *)base, (typename PG::Chunk *)gacc, g, parity, (typename P::Real)omega, variant);
+            count_launch();
+        }
+    }
+    static void gauge_identity(void *gacc, const Geom &g, cudaStream_t s)
+    {
+        k_gauge_identity<PG><<<blocks_for(2LL * g.Vh, 256), 256, 0, s>>>((typename PG::Chunk *)gacc, g);
+        count_launch();
+    }
+    static void gauge_reunitarize(void *gacc, const Geom &g, cudaStream_t s)
+    {
+        k_reunitarize<PG><<<blocks_for(2LL * g.Vh, 256), 256, 0, s>>>((typename PG::Chunk *)gacc, g, 2);
         count_launch();
     }
     static int unitarity_partials(const void *base, const Geom &g, double2 *partials, cudaStream_t s)
@@ -78,6 +104,11 @@ template <class P> struct OpsImpl {
         o.theta_partials = theta_partials;
         o.plaq_partials = plaq_partials;
         o.reunitarize = reunitarize;
+        o.halfsweep_acc = kFP32 ? halfsweep_acc : nullptr;
+        o.gauge_identity = kFP32 ? gauge_identity : nullptr;
+        o.gauge_reunitarize = kFP32 ? gauge_reunitarize : nullptr;
+        o.gauge_nchunk = kFP32 ? PG::NCHUNK : 0;
+        o.gauge_chunk_bytes = (int)sizeof(typename PG::Chunk);
         o.unitarity_partials = unitarity_partials;
         o.to_internal_d = to_internal_d;
         o.to_internal_f = to_internal_f;

@@ -19,4 +19,19 @@ void launch_widen(const Ops *from, const void *src, const Ops *to, void *dst, co
         k_widen<Param<2, float, 4>, Param<2, double, 4>><<<nb, 256, 0, s>>>((const float4 *)src, (double2 *)dst, g);
     count_launch();
 }
+void launch_rotate_orbit(const Ops *from, const void *gacc, const Ops *to, void *base64, const Geom &g,
+                         cudaStream_t s)
+{
+    unsigned nb = blocks_for(8LL * g.Vh, 128);
+    if (from->nc == 3 && to->nreal == 18)
+        k_rotate_orbit<Param<3, float, 12>, Param<3, double, 18>>
+            <<<nb, 128, 0, s>>>((const float4 *)gacc, (double2 *)base64, g);
+    else if (from->nc == 3 && to->nreal == 12)
+        k_rotate_orbit<Param<3, float, 12>, Param<3, double, 12>>
+            <<<nb, 128, 0, s>>>((const float4 *)gacc, (double2 *)base64, g);
+    else if (from->nc == 2)
+        k_rotate_orbit<Param<2, float, 4>, Param<2, double, 4>>
+            <<<nb, 128, 0, s>>>((const float4 *)gacc, (double2 *)base64, g);
+    count_launch();
+}
 } // namespace culgt
