@@ -51,7 +51,8 @@ typedef enum {
     CULGT_ERR_CUDA = -4,      /* a CUDA runtime call failed */
     CULGT_ERR_OOM = -5,       /* device allocation failed */
     CULGT_ERR_NONFINITE = -6, /* theta or F came out NaN/Inf (corrupt links) */
-    CULGT_ERR_TIMEOUT = -7    /* a bounded device-side wait gave up */
+    CULGT_ERR_TIMEOUT = -7,   /* a bounded device-side wait gave up */
+    CULGT_ERR_TOO_LARGE = -8  /* lattice larger than culgt_theta_static_scratch's fixed scratch */
 } culgt_status;
 
 typedef enum { CULGT_FP64 = 0, CULGT_FP32 = 1, CULGT_MIXED = 2 } culgt_precision;
@@ -151,6 +152,27 @@ culgt_status culgt_sweep(void *d_links, const culgt_params *p, int n_sweeps, voi
 
 /* theta and F of d_links (either pointer may be NULL). */
 culgt_status culgt_theta(const void *d_links, const culgt_params *p, void *cuda_stream, double *theta, double *F);
+
+/* theta and F like culgt_theta, for callers that cannot allocate device
+ * memory while they run: a host program that has given the whole GPU to its
+ * own memory pool (cudaMalloc would fail or fragment that pool), or a
+ * stream-ordered loop that cannot take the device-wide synchronisation that
+ * cudaMalloc/cudaFree may cause. This call allocates nothing: it reads the
+ * canonical links in place and keeps its per-block partial sums in a fixed
+ * device array inside the library (256 KB; every GPU that loads the library
+ * holds it until the process exits). The paper has no counterpart; it is an
+ * interface convenience of this library.
+ *   d_links  canonical links (device), as for culgt_theta; theta and F are
+ *            formed in FP64 whatever dtype_in is.
+ *   d_out    device buffer of two doubles: d_out[0] = theta, d_out[1] = F,
+ *            written in stream order (the call does not synchronise).
+ * Lattices above 4,194,304 sites return CULGT_ERR_TOO_LARGE before any
+ * device work. The first call on a device looks up the array's device
+ * address with that device current; make that first call before any stream
+ * capture. All calls share the array: calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller. */
+culgt_status culgt_theta_static_scratch(const void *d_links, const culgt_params *p, void *cuda_stream,
+                                        double *d_out);
 
 /* Average plaquette (1/(6 Nc V)) sum_x sum_{mu<nu} Re tr[U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+]. */
 culgt_status culgt_plaquette(const void *d_links, const culgt_params *p, void *cuda_stream, double *plaq);

@@ -256,6 +256,8 @@ const char *culgt_status_string(int status)
     case CULGT_ERR_OOM: return "CULGT_ERR_OOM: device allocation failed";
     case CULGT_ERR_NONFINITE: return "CULGT_ERR_NONFINITE: theta or F is not finite";
     case CULGT_ERR_TIMEOUT: return "CULGT_ERR_TIMEOUT: a bounded device-side wait gave up";
+    case CULGT_ERR_TOO_LARGE:
+        return "CULGT_ERR_TOO_LARGE: lattice above the 4,194,304 sites culgt_theta_static_scratch supports";
     default: return "unknown culgt status";
     }
 }

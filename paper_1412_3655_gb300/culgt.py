@@ -19,6 +19,7 @@ LIBRARY_PATH = os.path.join(_HERE, "libculgt.so")
 
 OK, NOT_CONVERGED = 0, 1
 ERR_ARG, ERR_DIMS, ERR_NC, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_TIMEOUT = -1, -2, -3, -4, -5, -6, -7
+ERR_TOO_LARGE = -8
 FP64, FP32, MIXED = 0, 1, 2
 
 
@@ -139,6 +140,7 @@ def library():
         "culgt_sweep": (ip, [vp, P, ip, vp]),
         "culgt_theta": (ip, [vp, P, vp, dp, dp]),
         "culgt_plaquette": (ip, [vp, P, vp, dp]),
+        "culgt_theta_static_scratch": (ip, [vp, P, vp, vp]),
         "culgt_reunitarize": (ip, [vp, P, vp]),
     }
     for name, (res, args) in sigs.items():
@@ -233,6 +235,18 @@ def culgt_theta(links, params: Params, stream=None):
     _check(library().culgt_theta(_links_ptr(links, params, True), ctypes.byref(params._c()), _stream(stream),
                                  ctypes.byref(th), ctypes.byref(F)), "culgt_theta")
     return th.value, F.value
+
+
+def culgt_theta_static_scratch(links, params: Params, out, stream=None) -> None:
+    """theta and F into the CUDA float64 tensor `out` (2 elements), stream-ordered,
+    for callers that cannot allocate device memory: the library keeps the
+    partial sums in a fixed device array (lattices up to 4,194,304 sites)."""
+    import torch
+    if not (out.is_cuda and out.dtype == torch.float64 and out.numel() >= 2 and out.is_contiguous()):
+        raise ValueError("out must be a contiguous CUDA float64 tensor with 2 elements")
+    _check(library().culgt_theta_static_scratch(_links_ptr(links, params, True), ctypes.byref(params._c()),
+                                                _stream(stream), ctypes.c_void_p(out.data_ptr())),
+           "culgt_theta_static_scratch")
 
 
 def culgt_plaquette(links, params: Params, stream=None) -> float:
