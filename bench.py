@@ -44,8 +44,15 @@ WORKLOADS = {
 }
 
 # algorithmic bytes per site update: 8 links read + 8 written
+# algorithmic FP64 flops per site update (FMA = 2): SU(3) = gather 126 +
+# subgroup steps 108 + row rotations 336 + eight 3x3 complex products 1584
+FLOPS_PER_SITE = {3: 2154, 2: 282}
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
+
 BYTES_PER_SITE = {(3, 1, 12): 768, (3, 1, 18): 1152, (3, 0, 18): 2304, (3, 0, 12): 1536,
-                  (2, 1, 4): 256, (2, 0, 4): 512}
+                  (2, 1, 4): 256, (2, 0, 4): 512,
+                  # FP32 phase of the mixed schedule: plus the site's own accumulated g, read and written
+                  (3, 1, 12, "acc"): 768 + 96, (2, 1, 4, "acc"): 256 + 32}
 
 
 def parse():
@@ -56,6 +63,11 @@ def parse():
     ap.add_argument("--impl", default="culgt", choices=["culgt", "reference"])
     ap.add_argument("--workload", default="su3_32x32x32x32", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-step", choices=["mixed", "fp64", "fp32"], default=None,
+                    help="run one gauge fixing (or --profile-sweeps sweeps) of the workload and exit; "
+                         "the command the ncu captures in profiles/ wrap")
+    ap.add_argument("--profile-sweeps", type=int, default=0,
+                    help="with --profile-step: this many sweeps instead of a whole fix")
     return ap.parse_args()
 
 
@@ -205,6 +217,36 @@ def run_reference(args):
     return 0
 
 
+def run_profile_step(args):
+    """One step of the chosen schedule, nothing else: what the ncu captures wrap."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1412_3655_gb300 import culgt, synth
+    dims, nc, eps, seed, omega = WORKLOADS[args.workload]
+    U = synth.gauge_config(dims, nc, eps, seed)
+    d_in = torch.from_numpy(U.view(np.float64).copy()).cuda()
+    d_out = torch.empty_like(d_in)
+    prec = {"mixed": culgt.MIXED, "fp64": culgt.FP64, "fp32": culgt.FP32}[args.profile_step]
+    p = culgt.Params.defaults(nc, dims, omega=omega, precision=prec, check_every=10, reunit_every=50,
+                              max_sweeps=20000)
+    with culgt.Handle(p) as h:
+        h.culgt_load(d_in)
+        if args.profile_sweeps:
+            h.culgt_handle_sweep(args.profile_sweeps)
+            th, F = h.culgt_handle_theta()
+            out = {"sweeps": args.profile_sweeps, "theta": th, "F": F}
+        else:
+            r = h.culgt_handle_fix()
+            out = {"sweeps_fp32": r.sweeps_fp32, "sweeps_fp64": r.sweeps_fp64, "theta": r.theta, "F": r.F}
+        h.culgt_store(d_out)
+        torch.cuda.synchronize()
+    print(json.dumps({"profile_step": args.profile_step, "workload": args.workload, **out}), flush=True)
+    return 0
+
+
 def run_culgt(args):
     import numpy as np
     import torch
@@ -285,26 +327,39 @@ def run_culgt(args):
             torch.cuda.synchronize()
             return a.elapsed_time(b) / (2 * n_sweeps)
 
-    p32 = culgt.Params.defaults(nc, dims, omega=omega, precision=culgt.FP32)
-    t32 = kernel_ms(p32)
+    # the FP32 phase kernel of the mixed schedule (it also accumulates g)
+    t32 = kernel_ms(mixed)
     t64 = kernel_ms(plain, 20)
     peaks, peak_src = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
     share32 = last.sweeps_fp32 * t32
     share64 = last.sweeps_fp64 * t64
 
-    def roofline(key, t_ms):
+    def roofline_hbm(key, t_ms):
         bytes_launch = (V // 2) * BYTES_PER_SITE[key]
         achieved = bytes_launch / (t_ms / 1e3) / 1e9
+        name = f"halfsweep_su{nc}_{'f32' if key[1] else 'f64'}_{key[2]}" + ("_acc" if len(key) > 3 else "")
         return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": recorded_traffic(f"halfsweep_su{nc}_{'f32' if key[1] else 'f64'}_{key[2]}"),
-                "kernel": f"k_halfsweep SU({nc}) {'FP32' if key[1] else 'FP64'} {key[2]}-real",
-                "launch_ms": t_ms, "algorithmic_bytes_per_launch": bytes_launch,
-                "peak_source": f"{peak_src} hbm_gbs"}
+                "traffic": recorded_traffic(name), "kernel": name, "launch_ms": t_ms,
+                "algorithmic_bytes_per_launch": bytes_launch, "peak_source": f"{peak_src} hbm_gbs"}
 
-    rl32 = roofline((nc, 1, 12), t32)
-    rl64 = roofline((nc, 0, 18), t64)
+    def roofline_fp64(key, t_ms):
+        # FP64-ALU bound on GB300: algorithmic FP64 flops per SU(3) site update
+        # (FMA = 2) against 2 DFMA/clock/SM x 152 SMs x 2070 MHz
+        flops_launch = (V // 2) * FLOPS_PER_SITE[nc]
+        achieved = flops_launch / (t_ms / 1e3) / 1e12
+        name = f"halfsweep_su{nc}_{'f32' if key[1] else 'f64'}_{key[2]}"
+        return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(name), "kernel": name,
+                "launch_ms": t_ms, "algorithmic_flops_per_launch": flops_launch,
+                "algorithmic_bytes_per_launch": (V // 2) * BYTES_PER_SITE[key],
+                "hbm_frac": (V // 2) * BYTES_PER_SITE[key] / (t_ms / 1e3) / 1e9 / hbm,
+                "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (unit counts and max clock)"}
+
+    rl32 = roofline_hbm((nc, 1, 12 if nc == 3 else 4, "acc"), t32)
+    rl64 = roofline_fp64((nc, 0, 18 if nc == 3 else 4), t64)
     dominant = rl32 if share32 >= share64 else rl64
+    dominant = dict(dominant, time_share_in_step=max(share32, share64) / max(share32 + share64, 1e-30))
 
     # plain FP64 time to theta < 1e-12 on the same input
     hp = culgt.Handle(plain, stream)
@@ -344,7 +399,7 @@ def run_culgt(args):
         "time_to_theta": {"mixed_s": ms / args.steps / 1e3, "fp64_s": fp64_ms / 1e3,
                           "fp64_sweeps": rp.sweeps_fp64, "fp64_F": rp.F, "mixed_F": last.F},
         "roofline": dominant,
-        "roofline_kernels": {"fp32_12": rl32, "fp64_18": rl64},
+        "roofline_kernels": {"fp32_phase": rl32, "fp64": rl64},
         "gpu_launches": launches,
         "e2e": {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": canon_bytes,
                 "d2h_bytes_per_step": canon_bytes, "steps": n_e2e},
@@ -364,6 +419,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_step:
+        return run_profile_step(args)
     return run_culgt(args)
 
 

@@ -131,10 +131,14 @@ culgt_status theta_now(culgt_handle *h, double *theta, double *F)
     return CULGT_OK;
 }
 
-culgt_status plaquette_now(culgt_handle *h, double *P)
+// of the current links, or with fp64 = true of the FP64 buffer (a mixed
+// handle's FP64 input before the switch)
+culgt_status plaquette_now(culgt_handle *h, double *P, bool fp64 = false)
 {
     const Geom &g = h->geom;
-    int nb = cur_ops(h)->plaq_partials(cur_buf(h), g, h->partials, h->stream);
+    const Ops *o = fp64 ? h->ops64 : cur_ops(h);
+    const void *b = fp64 ? h->buf64 : cur_buf(h);
+    int nb = o->plaq_partials(b, g, h->partials, h->stream);
     launch_finalize2(h->partials, nb, 1.0 / (6.0 * h->prm.nc * g.V), 0.0, h->d_scalars, h->stream);
     ST(sync_scalars(h, 1));
     *P = h->h_scalars[0];
@@ -228,7 +232,7 @@ culgt_status fix_call(culgt_handle *h, const void *d_in, void *d_out, culgt_resu
     culgt_result r;
     std::memset(&r, 0, sizeof r);
     ST(culgt_load(h, d_in));
-    ST(plaquette_now(h, &r.plaq_before));
+    ST(plaquette_now(h, &r.plaq_before, h->buf64 != nullptr));
     culgt_status st = fix_handle(h, &r);
     if (st < 0) return st;
     ST(plaquette_now(h, &r.plaq_after));

@@ -126,43 +126,70 @@ template <typename T> __device__ __forceinline__ void m3_acc_adj(M3<T> &acc, con
         }
 }
 
-// c = a b
-template <typename T> __device__ __forceinline__ void m3_mul(M3<T> &c, const M3<T> &a, const M3<T> &b)
+// Complex 3x3 products written as explicit fused multiply-add chains: one
+// multiply and five FMAs per real output (a separate add per term would cost
+// a third more FP64 instructions, and FP64 is GB300's scarce pipe).
+
+// rows R0..R1 of c = a b  (R1 = 2: the full product)
+template <int R0, int R1, typename T>
+__device__ __forceinline__ void m3_mul_rows(M3<T> &c, const M3<T> &a, const M3<T> &b)
 {
 #pragma unroll
-    for (int i = 0; i < 3; i++)
+    for (int i = R0; i <= R1; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            T sr = a.re[i][0] * b.re[0][j] - a.im[i][0] * b.im[0][j];
-            T si = a.re[i][0] * b.im[0][j] + a.im[i][0] * b.re[0][j];
-#pragma unroll
-            for (int k = 1; k < 3; k++) {
-                sr += a.re[i][k] * b.re[k][j] - a.im[i][k] * b.im[k][j];
-                si += a.re[i][k] * b.im[k][j] + a.im[i][k] * b.re[k][j];
-            }
+            T sr = a.re[i][0] * b.re[0][j];
+            sr = fma(-a.im[i][0], b.im[0][j], sr);
+            sr = fma(a.re[i][1], b.re[1][j], sr);
+            sr = fma(-a.im[i][1], b.im[1][j], sr);
+            sr = fma(a.re[i][2], b.re[2][j], sr);
+            sr = fma(-a.im[i][2], b.im[2][j], sr);
+            T si = a.re[i][0] * b.im[0][j];
+            si = fma(a.im[i][0], b.re[0][j], si);
+            si = fma(a.re[i][1], b.im[1][j], si);
+            si = fma(a.im[i][1], b.re[1][j], si);
+            si = fma(a.re[i][2], b.im[2][j], si);
+            si = fma(a.im[i][2], b.re[2][j], si);
             c.re[i][j] = sr;
             c.im[i][j] = si;
         }
 }
 
-// c = a b^+
-template <typename T> __device__ __forceinline__ void m3_mul_adj(M3<T> &c, const M3<T> &a, const M3<T> &b)
+// rows R0..R1 of c = a b^+, (a b^+)_ij = sum_k a_ik conj(b_jk)
+template <int R0, int R1, typename T>
+__device__ __forceinline__ void m3_mul_adj_rows(M3<T> &c, const M3<T> &a, const M3<T> &b)
 {
 #pragma unroll
-    for (int i = 0; i < 3; i++)
+    for (int i = R0; i <= R1; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            // sum_k a_ik conj(b_jk)
-            T sr = a.re[i][0] * b.re[j][0] + a.im[i][0] * b.im[j][0];
-            T si = a.im[i][0] * b.re[j][0] - a.re[i][0] * b.im[j][0];
-#pragma unroll
-            for (int k = 1; k < 3; k++) {
-                sr += a.re[i][k] * b.re[j][k] + a.im[i][k] * b.im[j][k];
-                si += a.im[i][k] * b.re[j][k] - a.re[i][k] * b.im[j][k];
-            }
+            T sr = a.re[i][0] * b.re[j][0];
+            sr = fma(a.im[i][0], b.im[j][0], sr);
+            sr = fma(a.re[i][1], b.re[j][1], sr);
+            sr = fma(a.im[i][1], b.im[j][1], sr);
+            sr = fma(a.re[i][2], b.re[j][2], sr);
+            sr = fma(a.im[i][2], b.im[j][2], sr);
+            T si = a.im[i][0] * b.re[j][0];
+            si = fma(-a.re[i][0], b.im[j][0], si);
+            si = fma(a.im[i][1], b.re[j][1], si);
+            si = fma(-a.re[i][1], b.im[j][1], si);
+            si = fma(a.im[i][2], b.re[j][2], si);
+            si = fma(-a.re[i][2], b.im[j][2], si);
             c.re[i][j] = sr;
             c.im[i][j] = si;
         }
+}
+
+// c = a b
+template <typename T> __device__ __forceinline__ void m3_mul(M3<T> &c, const M3<T> &a, const M3<T> &b)
+{
+    m3_mul_rows<0, 2>(c, a, b);
+}
+
+// c = a b^+
+template <typename T> __device__ __forceinline__ void m3_mul_adj(M3<T> &c, const M3<T> &a, const M3<T> &b)
+{
+    m3_mul_adj_rows<0, 2>(c, a, b);
 }
 
 // row 2 = conj(row 0 x row 1): the third row of an SU(3) matrix from its
@@ -172,8 +199,15 @@ template <typename T> __device__ __forceinline__ void m3_rebuild_row2(M3<T> &u)
 #pragma unroll
     for (int b = 0; b < 3; b++) {
         const int c = (b + 1) % 3, d = (b + 2) % 3;
-        T xr = u.re[0][c] * u.re[1][d] - u.im[0][c] * u.im[1][d] - (u.re[0][d] * u.re[1][c] - u.im[0][d] * u.im[1][c]);
-        T xi = u.re[0][c] * u.im[1][d] + u.im[0][c] * u.re[1][d] - (u.re[0][d] * u.im[1][c] + u.im[0][d] * u.re[1][c]);
+        // x = r0_c r1_d - r0_d r1_c, row2_b = conj(x)
+        T xr = u.re[0][c] * u.re[1][d];
+        xr = fma(-u.im[0][c], u.im[1][d], xr);
+        xr = fma(-u.re[0][d], u.re[1][c], xr);
+        xr = fma(u.im[0][d], u.im[1][c], xr);
+        T xi = u.re[0][c] * u.im[1][d];
+        xi = fma(u.im[0][c], u.re[1][d], xi);
+        xi = fma(-u.re[0][d], u.im[1][c], xi);
+        xi = fma(-u.im[0][d], u.re[1][c], xi);
         u.re[2][b] = xr;
         u.im[2][b] = -xi;
     }
@@ -252,13 +286,13 @@ __device__ __forceinline__ void su2_or_step(T a0, T a1, T a2, T a3, T omega, int
         q[1] = q[2] = q[3] = T(0);
         return;
     }
-    T inv = T(1) / sqrt(n2);
+    T inv = rsqrt(n2);
     T c0 = a0 * inv, c1 = -a1 * inv, c2 = -a2 * inv, c3 = -a3 * inv;
     if (variant == 0) {
         T beta = omega * (T(1) + (omega - T(1)) * (c0 - T(1)));
         T x0 = (T(1) - omega) + beta * c0;
         T x1 = beta * c1, x2 = beta * c2, x3 = beta * c3;
-        T m = T(1) / sqrt(x0 * x0 + x1 * x1 + x2 * x2 + x3 * x3);
+        T m = rsqrt(x0 * x0 + x1 * x1 + x2 * x2 + x3 * x3);
         q[0] = x0 * m;
         q[1] = x1 * m;
         q[2] = x2 * m;
@@ -287,10 +321,26 @@ template <typename T, int I, int J> __device__ __forceinline__ void rotate_rows(
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         T xr = m.re[I][c], xi = m.im[I][c], yr = m.re[J][c], yi = m.im[J][c];
-        m.re[I][c] = q[0] * xr - q[3] * xi + q[2] * yr - q[1] * yi;
-        m.im[I][c] = q[0] * xi + q[3] * xr + q[2] * yi + q[1] * yr;
-        m.re[J][c] = -q[2] * xr - q[1] * xi + q[0] * yr + q[3] * yi;
-        m.im[J][c] = -q[2] * xi + q[1] * xr + q[0] * yi - q[3] * yr;
+        T a = q[0] * xr;
+        a = fma(-q[3], xi, a);
+        a = fma(q[2], yr, a);
+        a = fma(-q[1], yi, a);
+        T b = q[0] * xi;
+        b = fma(q[3], xr, b);
+        b = fma(q[2], yi, b);
+        b = fma(q[1], yr, b);
+        T e = q[0] * yr;
+        e = fma(q[3], yi, e);
+        e = fma(-q[2], xr, e);
+        e = fma(-q[1], xi, e);
+        T f = q[0] * yi;
+        f = fma(-q[3], yr, f);
+        f = fma(-q[2], xi, f);
+        f = fma(q[1], xr, f);
+        m.re[I][c] = a;
+        m.im[I][c] = b;
+        m.re[J][c] = e;
+        m.im[J][c] = f;
     }
 }
 
@@ -326,7 +376,20 @@ template <typename T> __device__ __forceinline__ void su3_local_gauge(M3<T> &K, 
     block_quaternion<T, 0, 2>(K, a0, a1, a2, a3);
     su2_or_step(a0, a1, a2, a3, omega, variant, q);
     rotate_rows<T, 0, 2>(K, q);
-    rotate_rows<T, 0, 2>(g, q);
+    // g <- R02 g with g = R01 (row 2 = (0, 0, 1)): row 0 = n00 (g00, g01, 0) + n01 e2,
+    // row 2 = n10 (g00, g01, 0) + n11 e2, n = [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]]
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        T xr = g.re[0][c], xi = g.im[0][c];
+        g.re[0][c] = fma(-q[3], xi, q[0] * xr);
+        g.im[0][c] = fma(q[3], xr, q[0] * xi);
+        g.re[2][c] = fma(-q[1], xi, -q[2] * xr);
+        g.im[2][c] = fma(q[1], xr, -q[2] * xi);
+    }
+    g.re[0][2] = q[2];
+    g.im[0][2] = q[1];
+    g.re[2][2] = q[0];
+    g.im[2][2] = -q[3];
 
     block_quaternion<T, 1, 2>(K, a0, a1, a2, a3);
     su2_or_step(a0, a1, a2, a3, omega, variant, q);

@@ -22,6 +22,25 @@ template <class P> struct KeepLinks {
     static constexpr bool value = (sizeof(typename P::Real) * P::NREAL * 8 <= 4 * 12 * 8);
 };
 
+// The updated links: rows 0 and 1 by matrix product; for full (18-real)
+// storage row 2 is rebuilt as conj(row0 x row1), cheaper than a third row of
+// products and exact for SU(3); 12-real storage keeps rows 0 and 1 only.
+template <class P>
+__device__ __forceinline__ void apply_left(M3<typename P::Real> &t, const M3<typename P::Real> &G,
+                                           const M3<typename P::Real> &u)
+{
+    m3_mul_rows<0, 1>(t, G, u);
+    if constexpr (P::NREAL == 18) m3_rebuild_row2(t);
+}
+
+template <class P>
+__device__ __forceinline__ void apply_right_adj(M3<typename P::Real> &t, const M3<typename P::Real> &u,
+                                                const M3<typename P::Real> &G)
+{
+    m3_mul_adj_rows<0, 1>(t, u, G);
+    if constexpr (P::NREAL == 18) m3_rebuild_row2(t);
+}
+
 template <class P, bool KEEP>
 __device__ __forceinline__ void su3_site_update(typename P::Chunk *base, const Geom &g, int cb, int p, int mu_first,
                                                 typename P::Real omega, int variant, M3<typename P::Real> *gout)
@@ -60,9 +79,9 @@ __device__ __forceinline__ void su3_site_update(typename P::Chunk *base, const G
         for (int mu = 0; mu < 4; mu++) {
             if (mu < mu_first) continue;
             M3<T> t;
-            m3_mul(t, G, uf[mu]);
+            apply_left<P>(t, G, uf[mu]);
             P::store(fwd[mu], g.stride, t);
-            m3_mul_adj(t, ub[mu], G);
+            apply_right_adj<P>(t, ub[mu], G);
             P::store(bwd[mu], g.stride, t);
         }
         if (gout) *gout = G;
@@ -83,10 +102,10 @@ __device__ __forceinline__ void su3_site_update(typename P::Chunk *base, const G
             if (mu < mu_first) continue;
             M3<T> u, t;
             P::load(fwd[mu], g.stride, u);
-            m3_mul(t, G, u);
+            apply_left<P>(t, G, u);
             P::store(fwd[mu], g.stride, t);
             P::load(bwd[mu], g.stride, u);
-            m3_mul_adj(t, u, G);
+            apply_right_adj<P>(t, u, G);
             P::store(bwd[mu], g.stride, t);
         }
         if (gout) *gout = G;
