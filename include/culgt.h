@@ -147,6 +147,14 @@ culgt_status culgt_landau_fix(void *d_links, const culgt_params *p, void *cuda_s
  * device -> host copy, all inside the call. */
 culgt_status culgt_landau_fix_host(void *h_links, const culgt_params *p, void *cuda_stream, culgt_result *out);
 
+/* Coulomb gauge fixing in place: one 3D problem per time slice over mu =
+ * 1..3, each stopping at its own theta_t < theta_target; the accumulated
+ * transformation g(x) then rotates the temporal links once,
+ * U_0(x) <- g(x) U_0(x) g(x+0)^+. per_slice receives L0 results (may be NULL).
+ * d_gauge, if not NULL, receives g(x) as [V][Nc][Nc] complex double. */
+culgt_status culgt_coulomb_fix(void *d_links, const culgt_params *p, void *cuda_stream, culgt_result *per_slice,
+                               void *d_gauge);
+
 /* n_sweeps sweeps of d_links in place at the given precision. */
 culgt_status culgt_sweep(void *d_links, const culgt_params *p, int n_sweeps, void *cuda_stream);
 
@@ -180,6 +188,18 @@ culgt_status culgt_plaquette(const void *d_links, const culgt_params *p, void *c
 /* Reunitarisation of d_links in place (SU(3): Gram-Schmidt on rows 0, 1,
  * row 2 = conj(row0 x row1); SU(2): normalised quaternion part). */
 culgt_status culgt_reunitarize(void *d_links, const culgt_params *p, void *cuda_stream);
+
+/* ---- batched API: many independent problems, one launch per phase ------
+ * Problems may differ in dims; nc, precision, omega and the stopping rule
+ * come from *common (its dims are ignored). Each problem converges and
+ * retires on its own theta. out receives n results (may be NULL). */
+typedef struct {
+    void *d_links;  /* canonical links of this problem, device, dtype_in of *common */
+    int dims[4];
+} culgt_problem;
+
+culgt_status culgt_fix_batched(const culgt_problem *problems, int n, const culgt_params *common, void *cuda_stream,
+                               culgt_result *out);
 
 #ifdef __cplusplus
 }

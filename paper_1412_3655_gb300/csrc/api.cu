@@ -71,17 +71,6 @@ culgt_status validate(const culgt_params *p)
     return CULGT_OK;
 }
 
-Geom make_geom(const int *dims)
-{
-    Geom g;
-    for (int mu = 0; mu < 4; mu++) g.L[mu] = dims[mu];
-    g.half1 = dims[1] / 2;
-    g.V = dims[0] * dims[1] * dims[2] * dims[3];
-    g.Vh = g.V / 2;
-    g.stride = ((size_t)g.Vh + 63) / 64 * 64;
-    return g;
-}
-
 size_t buffer_bytes(const Ops *o, const Geom &g) { return (size_t)8 * o->nchunk * g.stride * o->chunk_bytes; }
 
 void pick_ops(const culgt_params *p, const Ops **o32, const Ops **o64)

@@ -1,0 +1,135 @@
+// Launch wrappers of the batched engine for one link parameterisation P;
+// included by batched_su3.cu and batched_su2.cu.
+#pragma once
+
+#include "batched.cuh"
+#include "launch.h"
+
+namespace culgt {
+
+// the kernels of one precision phase of the batched engine
+struct BPhaseOps {
+    int fp32;
+    // one colour of a half-sweep over every problem in `phase`; acc: also accumulate g
+    void (*sweep)(const BProb *probs, const int *map, int ntiles, int colour, int phase, double omega, int variant,
+                  bool acc, cudaStream_t s);
+    void (*theta)(const BProb *probs, const int *map, int ntiles, int phase, int only_switched, double2 *partials,
+                  cudaStream_t s);
+    void (*reunit)(const BProb *probs, const int *map, int ntiles, int phase, bool acc, cudaStream_t s);
+    // whole-lattice helpers: temporal links rotated by the accumulator; accumulator = 1
+    void (*temporal)(void *links, const void *gacc, const Geom &g, cudaStream_t s);
+    void (*gauge_identity)(void *gacc, const Geom &g, cudaStream_t s);
+    // FP64 phase only: the orbit-exact switch of problems in PH_SWITCH (acc64: also set gacc64)
+    void (*rotate)(const BProb *probs, const int *map, int ntiles, bool acc64, cudaStream_t s);
+    int acc_nchunk;       // chunks per site of this precision's accumulator
+    int acc_chunk_bytes;
+};
+
+const BPhaseOps *get_bops(int nc, int fp32, int nreal);
+
+extern const BPhaseOps bops_su3_f12, bops_su3_f18, bops_su3_d18, bops_su3_d12, bops_su2_f4, bops_su2_d4;
+
+// an accumulator (internal layout) -> [V][Nc][Nc] complex double, canonical site order
+void launch_gauge_to_canonical(int nc, int fp32, const void *gacc, double *out, const Geom &g, cudaStream_t s);
+
+template <class PG> __global__ void __launch_bounds__(256) k_gauge_to_canonical(const typename PG::Chunk *gacc,
+                                                                               double *out, Geom g)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    int x[4];
+    x[1] = i % g.L[1];
+    int r = i / g.L[1];
+    x[2] = r % g.L[2];
+    r /= g.L[2];
+    x[3] = r % g.L[3];
+    x[0] = r / g.L[3];
+    int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+    typename PG::Link u;
+    PG::load(gacc + (size_t)p * PG::NCHUNK * g.stride + (i >> 1), g.stride, u);
+    double *o = out + (size_t)i * 2 * PG::NC * PG::NC;
+    if constexpr (PG::NC == 3) {
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            o[2 * k] = (double)u.re[k / 3][k % 3];
+            o[2 * k + 1] = (double)u.im[k / 3][k % 3];
+        }
+    } else {
+        o[0] = u.a[0]; o[1] = u.a[3]; o[2] = u.a[2]; o[3] = u.a[1];
+        o[4] = -u.a[2]; o[5] = u.a[1]; o[6] = u.a[0]; o[7] = -u.a[3];
+    }
+}
+
+// accumulator storage: two rows (SU(3)) or a quaternion (SU(2)), in P's precision
+template <class P> struct AccParam {
+    typedef Param<P::NC, typename P::Real, P::NC == 3 ? 12 : 4> type;
+};
+
+template <class P> struct BImpl {
+    typedef typename AccParam<P>::type PG;
+    typedef Param<P::NC, float, P::NC == 3 ? 12 : 4> PG32;
+    static constexpr bool kFP32 = sizeof(typename P::Real) == 4;
+
+    static void sweep(const BProb *probs, const int *map, int ntiles, int colour, int phase, double omega,
+                      int variant, bool acc, cudaStream_t s)
+    {
+        if (acc)
+            k_b_halfsweep<P, PG><<<ntiles, kSweepTile, 0, s>>>(probs, map, colour, phase, omega, variant);
+        else
+            k_b_halfsweep<P, void><<<ntiles, kSweepTile, 0, s>>>(probs, map, colour, phase, omega, variant);
+        count_launch();
+    }
+    static void theta(const BProb *probs, const int *map, int ntiles, int phase, int only_switched,
+                      double2 *partials, cudaStream_t s)
+    {
+        k_b_theta<P><<<ntiles, kThetaTile, 0, s>>>(probs, map, phase, only_switched, partials);
+        count_launch();
+    }
+    static void reunit(const BProb *probs, const int *map, int ntiles, int phase, bool acc, cudaStream_t s)
+    {
+        if (acc)
+            k_b_reunitarize<P, PG><<<ntiles, kThetaTile, 0, s>>>(probs, map, phase);
+        else
+            k_b_reunitarize<P, void><<<ntiles, kThetaTile, 0, s>>>(probs, map, phase);
+        count_launch();
+    }
+    static void temporal(void *links, const void *gacc, const Geom &g, cudaStream_t s)
+    {
+        unsigned nb = (unsigned)((2LL * g.Vh + kThetaTile - 1) / kThetaTile);
+        k_temporal_rotate<P, PG><<<nb, kThetaTile, 0, s>>>((typename P::Chunk *)links,
+                                                           (const typename PG::Chunk *)gacc, g);
+        count_launch();
+    }
+    static void gauge_identity(void *gacc, const Geom &g, cudaStream_t s)
+    {
+        unsigned nb = (unsigned)((2LL * g.Vh + 255) / 256);
+        k_gauge_identity<PG><<<nb, 256, 0, s>>>((typename PG::Chunk *)gacc, g);
+        count_launch();
+    }
+    static void rotate(const BProb *probs, const int *map, int ntiles, bool acc64, cudaStream_t s)
+    {
+        if constexpr (!kFP32) {
+            if (acc64)
+                k_b_rotate<PG32, P, PG><<<ntiles, kThetaTile, 0, s>>>(probs, map);
+            else
+                k_b_rotate<PG32, P, void><<<ntiles, kThetaTile, 0, s>>>(probs, map);
+            count_launch();
+        }
+    }
+    static BPhaseOps make()
+    {
+        BPhaseOps o;
+        o.fp32 = kFP32;
+        o.sweep = sweep;
+        o.theta = theta;
+        o.reunit = reunit;
+        o.temporal = temporal;
+        o.gauge_identity = gauge_identity;
+        o.rotate = kFP32 ? nullptr : rotate;
+        o.acc_nchunk = PG::NCHUNK;
+        o.acc_chunk_bytes = (int)sizeof(typename PG::Chunk);
+        return o;
+    }
+};
+
+} // namespace culgt

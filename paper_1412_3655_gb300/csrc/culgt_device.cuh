@@ -17,6 +17,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace culgt {
 
 struct Geom {
@@ -249,6 +251,8 @@ template <typename T> __device__ __forceinline__ void m3_reunitarize(M3<T> &u)
     m3_rebuild_row2(u);
 }
 
+template <typename T> __device__ __forceinline__ void reunitarize_link(M3<T> &u) { m3_reunitarize(u); }
+
 // quaternion product (a0 + i a.s)(b0 + i b.s) = (a0 b0 - a.b) + i (a0 b + b0 a - a x b).s
 template <typename T> __device__ __forceinline__ Q4<T> q_mul(const Q4<T> &a, const Q4<T> &b)
 {
@@ -258,6 +262,13 @@ template <typename T> __device__ __forceinline__ Q4<T> q_mul(const Q4<T> &a, con
     c.a[2] = a.a[0] * b.a[2] + b.a[0] * a.a[2] - (a.a[3] * b.a[1] - a.a[1] * b.a[3]);
     c.a[3] = a.a[0] * b.a[3] + b.a[0] * a.a[3] - (a.a[1] * b.a[2] - a.a[2] * b.a[1]);
     return c;
+}
+
+template <typename T> __device__ __forceinline__ void reunitarize_link(Q4<T> &u)
+{
+    T n = rsqrt(u.a[0] * u.a[0] + u.a[1] * u.a[1] + u.a[2] * u.a[2] + u.a[3] * u.a[3]);
+#pragma unroll
+    for (int k = 0; k < 4; k++) u.a[k] *= n;
 }
 
 // a b^+ (b^+ = (b0, -b))

@@ -8,6 +8,18 @@
 
 namespace culgt {
 
+// geometry of an L0 x L1 x L2 x L3 lattice in the internal layout
+inline Geom make_geom(const int *dims)
+{
+    Geom g;
+    for (int mu = 0; mu < 4; mu++) g.L[mu] = dims[mu];
+    g.half1 = dims[1] / 2;
+    g.V = dims[0] * dims[1] * dims[2] * dims[3];
+    g.Vh = g.V / 2;
+    g.stride = ((size_t)g.Vh + 63) / 64 * 64;
+    return g;
+}
+
 struct Ops {
     int nc;         // 2 or 3
     int nreal;      // reals per link in device memory

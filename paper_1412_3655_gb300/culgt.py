@@ -59,6 +59,10 @@ class _Result(ctypes.Structure):
     ]
 
 
+class _Problem(ctypes.Structure):
+    _fields_ = [("d_links", ctypes.c_void_p), ("dims", ctypes.c_int * 4)]
+
+
 @dataclass
 class Params:
     """Mirror of culgt_params (see include/culgt.h for every field)."""
@@ -141,6 +145,8 @@ def library():
         "culgt_theta": (ip, [vp, P, vp, dp, dp]),
         "culgt_plaquette": (ip, [vp, P, vp, dp]),
         "culgt_theta_static_scratch": (ip, [vp, P, vp, vp]),
+        "culgt_coulomb_fix": (ip, [vp, P, vp, R, vp]),
+        "culgt_fix_batched": (ip, [ctypes.POINTER(_Problem), ip, P, vp, R]),
         "culgt_reunitarize": (ip, [vp, P, vp]),
     }
     for name, (res, args) in sigs.items():
@@ -223,6 +229,46 @@ def culgt_landau_fix_host(links, params: Params, stream=None) -> Result:
     st = _check(library().culgt_landau_fix_host(_links_ptr(links, params, False), ctypes.byref(params._c()),
                                                 _stream(stream), ctypes.byref(r)), "culgt_landau_fix_host")
     return Result._from(r, st)
+
+
+def culgt_coulomb_fix(links, params: Params, stream=None, gauge=None):
+    """Coulomb gauge fixing in place, one problem per time slice. Returns one
+    Result per slice (status on each). gauge: optional CUDA float64 tensor of
+    V * Nc * Nc * 2 elements that receives g(x)."""
+    nt = int(params.dims[0])
+    rs = (_Result * nt)()
+    gp = None
+    if gauge is not None:
+        import torch
+        V = 1
+        for d in params.dims:
+            V *= int(d)
+        real = torch.view_as_real(gauge) if gauge.is_complex() else gauge
+        if not (gauge.is_cuda and real.dtype == torch.float64 and gauge.is_contiguous()
+                and real.numel() == V * params.nc * params.nc * 2):
+            raise ValueError("gauge must be a contiguous CUDA float64 tensor of V*Nc*Nc*2 reals")
+        gp = ctypes.c_void_p(gauge.data_ptr())
+    st = _check(library().culgt_coulomb_fix(_links_ptr(links, params, True), ctypes.byref(params._c()),
+                                            _stream(stream), rs, gp), "culgt_coulomb_fix")
+    return [Result._from(r, st) for r in rs]
+
+
+def culgt_fix_batched(links_list, dims_list, params: Params, stream=None):
+    """Landau gauge fixing of several independent lattices (each a CUDA tensor
+    in the canonical layout, dims from dims_list) in shared launches; nc,
+    precision and the stopping rule come from params. One Result per problem."""
+    n = len(links_list)
+    if n != len(dims_list) or n == 0:
+        raise ValueError("need one dims entry per link tensor")
+    probs = (_Problem * n)()
+    for i, (t, dims) in enumerate(zip(links_list, dims_list)):
+        pi = Params(**{**params.__dict__, "dims": tuple(int(d) for d in dims)})
+        probs[i].d_links = _links_ptr(t, pi, True)
+        probs[i].dims = (ctypes.c_int * 4)(*[int(d) for d in dims])
+    rs = (_Result * n)()
+    st = _check(library().culgt_fix_batched(probs, n, ctypes.byref(params._c()), _stream(stream), rs),
+                "culgt_fix_batched")
+    return [Result._from(r, st) for r in rs]
 
 
 def culgt_sweep(links, params: Params, n_sweeps: int, stream=None) -> None:

@@ -169,18 +169,20 @@ def random_gauge(L, nc: int, seed: int, copy: int = 0) -> np.ndarray:
     return haar(sites, nc, seed, SLOT_G if copy == 0 else SLOT_COPY, copy)
 
 
-def gauge_config(L, nc: int, eps: float, seed: int, copy: int = 0, chunk: int = 1 << 18) -> np.ndarray:
+def gauge_config(L, nc: int, eps: float, seed: int, copy: int = 0, chunk: int = 1 << 18,
+                 spread: float | None = None) -> np.ndarray:
     """U_mu(x) = g(x) exp(i eps H_mu(x)) g(x+mu)^+ with Haar g, as (V, 4, Nc, Nc) complex128.
 
     copy > 0 returns the same configuration under a further Haar-random gauge
-    transformation (an independent starting point on the same gauge orbit)."""
+    transformation (an independent starting point on the same gauge orbit).
+    spread replaces the Haar g by g = exp(i spread H(x)), a gauge close to 1."""
     L = tuple(int(v) for v in L)
     if len(L) != 4 or any(v < 2 for v in L):
         raise ValueError("dims must be four extents >= 2")
     V = int(np.prod(L))
     T = generators(nc)
     ncoef = T.shape[0]
-    g = random_gauge(L, nc, seed, 0)
+    g = random_gauge(L, nc, seed, 0) if spread is None else near_identity_gauge(L, nc, seed, spread)
     U = np.empty((V, 4, nc, nc), dtype=np.complex128)
     for start in range(0, V, chunk):
         sites = np.arange(start, min(V, start + chunk), dtype=np.int64)
