@@ -63,11 +63,13 @@ def parse():
     ap.add_argument("--impl", default="culgt", choices=["culgt", "reference"])
     ap.add_argument("--workload", default="su3_32x32x32x32", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-step", choices=["mixed", "fp64", "fp32"], default=None,
+    ap.add_argument("--profile-step", choices=["mixed", "fp64", "fp32", "df", "mixed_df"], default=None,
                     help="run one gauge fixing (or --profile-sweeps sweeps) of the workload and exit; "
                          "the command the ncu captures in profiles/ wrap")
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="with --profile-step: this many sweeps instead of a whole fix")
+    ap.add_argument("--tps", type=int, default=0, help="with --profile-step: threads per site (0 = autotune)")
+    ap.add_argument("--block", type=int, default=0, help="with --profile-step: threads per block (0 = autotune)")
     return ap.parse_args()
 
 
@@ -76,6 +78,20 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def aggregate(ms_local, units_local, world_size, device=None):
+    """Whole-job figures over replicas: the slowest rank's time and the sum of
+    the ranks' site updates (the ranks run independent replicas)."""
+    if world_size <= 1:
+        return ms_local, units_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
 def measured_peaks():
@@ -229,9 +245,10 @@ def run_profile_step(args):
     U = synth.gauge_config(dims, nc, eps, seed)
     d_in = torch.from_numpy(U.view(np.float64).copy()).cuda()
     d_out = torch.empty_like(d_in)
-    prec = {"mixed": culgt.MIXED, "fp64": culgt.FP64, "fp32": culgt.FP32}[args.profile_step]
+    prec = {"mixed": culgt.MIXED, "fp64": culgt.FP64, "fp32": culgt.FP32, "df": culgt.DF,
+            "mixed_df": culgt.MIXED_DF}[args.profile_step]
     p = culgt.Params.defaults(nc, dims, omega=omega, precision=prec, check_every=10, reunit_every=50,
-                              max_sweeps=20000)
+                              max_sweeps=20000, threads_per_site=args.tps, block_size=args.block)
     with culgt.Handle(p) as h:
         h.culgt_load(d_in)
         if args.profile_sweeps:
@@ -307,19 +324,20 @@ def run_culgt(args):
     launches = culgt.culgt_kernel_launches() - launches0
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
     updates = sum((r.sweeps_fp32 + r.sweeps_fp64) * V for r in results)
-    value = updates * ws / (ms / 1e3)
+    ms, updates_all = aggregate(ms, updates, ws, dev)
+    value = updates_all / (ms / 1e3)
     last = results[-1]
 
     # per-kernel launch times: back-to-back half-sweeps on the launching stream
+    mapping = {}
+
     def kernel_ms(params, n_sweeps=100):
         with culgt.Handle(params, stream) as hk:
             hk.culgt_load(d_in)
             hk.culgt_handle_sweep(5)
+            mapping[{culgt.MIXED: "fp32_phase", culgt.FP64: "fp64", culgt.DF: "double_float"}.get(
+                params.precision, str(params.precision))] = hk.culgt_handle_tuning()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             hk.culgt_handle_sweep(n_sweeps)
@@ -335,20 +353,21 @@ def run_culgt(args):
     share32 = last.sweeps_fp32 * t32
     share64 = last.sweeps_fp64 * t64
 
-    def roofline_hbm(key, t_ms):
+    def roofline_hbm(key, t_ms, tps):
         bytes_launch = (V // 2) * BYTES_PER_SITE[key]
         achieved = bytes_launch / (t_ms / 1e3) / 1e9
-        name = f"halfsweep_su{nc}_{'f32' if key[1] else 'f64'}_{key[2]}" + ("_acc" if len(key) > 3 else "")
+        name = (f"halfsweep_su{nc}_{'f32' if key[1] else 'f64'}_{key[2]}" + ("_acc" if len(key) > 3 else "")
+                + f"_tps{tps}")
         return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": recorded_traffic(name), "kernel": name, "launch_ms": t_ms,
                 "algorithmic_bytes_per_launch": bytes_launch, "peak_source": f"{peak_src} hbm_gbs"}
 
-    def roofline_fp64(key, t_ms):
+    def roofline_fp64(key, t_ms, tps):
         # FP64-ALU bound on GB300: algorithmic FP64 flops per SU(3) site update
         # (FMA = 2) against 2 DFMA/clock/SM x 152 SMs x 2070 MHz
         flops_launch = (V // 2) * FLOPS_PER_SITE[nc]
         achieved = flops_launch / (t_ms / 1e3) / 1e12
-        name = f"halfsweep_su{nc}_{'f32' if key[1] else 'f64'}_{key[2]}"
+        name = f"halfsweep_su{nc}_{'f32' if key[1] else 'f64'}_{key[2]}_tps{tps}"
         return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(name), "kernel": name,
                 "launch_ms": t_ms, "algorithmic_flops_per_launch": flops_launch,
@@ -356,22 +375,40 @@ def run_culgt(args):
                 "hbm_frac": (V // 2) * BYTES_PER_SITE[key] / (t_ms / 1e3) / 1e9 / hbm,
                 "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (unit counts and max clock)"}
 
-    rl32 = roofline_hbm((nc, 1, 12 if nc == 3 else 4, "acc"), t32)
-    rl64 = roofline_fp64((nc, 0, 18 if nc == 3 else 4), t64)
+    rl32 = roofline_hbm((nc, 1, 12 if nc == 3 else 4, "acc"), t32, mapping["fp32_phase"][0])
+    rl64 = roofline_fp64((nc, 0, 18 if nc == 3 else 4), t64, mapping["fp64"][0])
     dominant = rl32 if share32 >= share64 else rl64
     dominant = dict(dominant, time_share_in_step=max(share32, share64) / max(share32 + share64, 1e-30))
 
-    # plain FP64 time to theta < 1e-12 on the same input
-    hp = culgt.Handle(plain, stream)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    hp.culgt_load(d_in)
-    rp = hp.culgt_handle_fix()
-    hp.culgt_store(d_out)
-    b.record(stream)
-    torch.cuda.synchronize()
-    fp64_ms = a.elapsed_time(b)
-    hp.close()
+    # time to theta < 1e-12 on the same input: plain FP64, and the double-float
+    # variants (FP64-size links as float pairs, FP32-pipe arithmetic, theta in FP64)
+    def fix_time(params):
+        hx = culgt.Handle(params, stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        hx.culgt_load(d_in)
+        r = hx.culgt_handle_fix()
+        hx.culgt_store(d_out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        hx.close()
+        return a.elapsed_time(b) / 1e3, r
+
+    fp64_s, rp = fix_time(plain)
+    mixed_df = culgt.Params(**{**mixed.__dict__, "precision": culgt.MIXED_DF})
+    only_df = culgt.Params(**{**plain.__dict__, "precision": culgt.DF})
+    mixed_df_s, rmd = fix_time(mixed_df)
+    df_s, rdf = fix_time(only_df)
+    tdf = kernel_ms(only_df, 20)
+    rldf = roofline_hbm((nc, 0, 18 if nc == 3 else 4), tdf, mapping["double_float"][0])
+    rldf["kernel"] = rldf["kernel"].replace("f64", "df")
+    rldf["traffic"] = recorded_traffic(rldf["kernel"])
+    # the FP32 -> FP64 switch later: the orbit-exact switch keeps the FP32
+    # rounding off the result, so the FP32 phase may run to a lower theta
+    late = {}
+    for sw in (1e-10, 1e-11):
+        t_sw, r_sw = fix_time(culgt.Params(**{**mixed.__dict__, "switch_theta": sw}))
+        late[f"{sw:g}"] = {"s": t_sw, "sweeps": [r_sw.sweeps_fp32, r_sw.sweeps_fp64], "F": r_sw.F, "theta": r_sw.theta}
 
     # end to end through the host entry point (pinned host buffer)
     pinned = host.pin_memory()
@@ -396,11 +433,18 @@ def run_culgt(args):
                    "check_every": 10, "reunit_every": 50, "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "inputs larger than L2 (FP32 links 201 MB, FP64 links 604 MB)"},
         "sweeps": {"fp32": last.sweeps_fp32, "fp64": last.sweeps_fp64, "theta": last.theta, "F": last.F},
-        "time_to_theta": {"mixed_s": ms / args.steps / 1e3, "fp64_s": fp64_ms / 1e3,
-                          "fp64_sweeps": rp.sweeps_fp64, "fp64_F": rp.F, "mixed_F": last.F},
+        "time_to_theta": {"mixed_s": ms / args.steps / 1e3, "fp64_s": fp64_s,
+                          "fp64_sweeps": rp.sweeps_fp64, "fp64_F": rp.F, "mixed_F": last.F,
+                          "mixed_df_s": mixed_df_s, "mixed_df_sweeps": [rmd.sweeps_fp32, rmd.sweeps_fp64],
+                          "mixed_df_F": rmd.F, "df_s": df_s, "df_sweeps": rdf.sweeps_fp64, "df_F": rdf.F,
+                          "mixed_switch_later": late,
+                          "note": "mixed: FP32 to theta<1e-8, then IEEE FP64 sweeps (the value above); *_df: "
+                                  "double-float sweeps (float pairs, ~48-bit) with theta/F in FP64; "
+                                  "mixed_switch_later: the same schedule with the FP32 phase run to a lower theta"},
         "roofline": dominant,
-        "roofline_kernels": {"fp32_phase": rl32, "fp64": rl64},
+        "roofline_kernels": {"fp32_phase": rl32, "fp64": rl64, "double_float": rldf},
         "gpu_launches": launches,
+        "sweep_mapping": {k: {"threads_per_site": v[0], "block": v[1]} for k, v in mapping.items()},
         "e2e": {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": canon_bytes,
                 "d2h_bytes_per_step": canon_bytes, "steps": n_e2e},
         "clocks": clocks,

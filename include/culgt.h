@@ -55,7 +55,16 @@ typedef enum {
     CULGT_ERR_TOO_LARGE = -8  /* lattice larger than culgt_theta_static_scratch's fixed scratch */
 } culgt_status;
 
-typedef enum { CULGT_FP64 = 0, CULGT_FP32 = 1, CULGT_MIXED = 2 } culgt_precision;
+/* Arithmetic of the sweeps. theta and F are always accumulated in FP64.
+ *   CULGT_FP64      IEEE FP64 links and arithmetic.
+ *   CULGT_FP32      FP32 links and arithmetic.
+ *   CULGT_MIXED     FP32 sweeps to switch_theta, then FP64 sweeps to theta_target.
+ *   CULGT_MIXED_DF  FP32 sweeps to switch_theta, then double-float sweeps: links
+ *                   kept as pairs of floats (hi + lo, ~48 bits, the size of FP64)
+ *                   and arithmetic on the FP32 pipes; theta and F formed in FP64
+ *                   from the stored pairs.
+ *   CULGT_DF        double-float sweeps throughout. */
+typedef enum { CULGT_FP64 = 0, CULGT_FP32 = 1, CULGT_MIXED = 2, CULGT_MIXED_DF = 3, CULGT_DF = 4 } culgt_precision;
 
 typedef struct {
     int dims[4];         /* L0 (time), L1, L2, L3; all even, >= 2 */
@@ -72,6 +81,8 @@ typedef struct {
     int reunit_every;    /* reunitarise after sweep n when n % reunit_every == 0; 0 = never */
     double switch_theta; /* mixed: leave the FP32 phase once theta < switch_theta */
     int dtype_in;        /* canonical link buffer element type: 0 = double, 1 = float */
+    int threads_per_site; /* half-sweep mapping: 1 or 2 threads per site; 0 = autotune */
+    int block_size;       /* half-sweep threads per block: 64, 128 or 256; 0 = autotune */
 } culgt_params;
 
 typedef struct {
@@ -133,6 +144,10 @@ culgt_status culgt_handle_reunitarize(culgt_handle *h);
  * culgt_load, so FP32 rounding never moves the links off the gauge orbit of
  * the input (the plaquette is kept to FP64 rounding). No-op in FP64. */
 culgt_status culgt_handle_to_fp64(culgt_handle *h);
+/* The half-sweep mapping the handle uses (after autotuning, which happens at
+ * the first sweep unless threads_per_site and block_size are both set). The
+ * mappings give bitwise identical links; only their speed differs. */
+culgt_status culgt_handle_tuning(culgt_handle *h, int *threads_per_site, int *block_size);
 /* Iterates to theta_target as the precision field says (mixed: FP32 until
  * theta < switch_theta, then FP64). Leaves the result in the handle. */
 culgt_status culgt_handle_fix(culgt_handle *h, culgt_result *out);

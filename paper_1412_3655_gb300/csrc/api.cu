@@ -5,7 +5,10 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 #include "../../include/culgt.h"
 #include "launch.h"
@@ -28,6 +31,7 @@ struct culgt_handle {
     void *staging;      // canonical device buffer for the host entry point
     void *gacc;         // mixed: FP32 accumulated gauge transformation per site
     int sweeps32, sweeps64;
+    int tps32, block32, tps64, block64;  // half-sweep mapping per precision (0 = not chosen yet)
 };
 
 namespace {
@@ -61,13 +65,16 @@ culgt_status validate(const culgt_params *p)
     if (V >= (1LL << 31) / 4) return CULGT_ERR_DIMS;
     if (!(p->omega >= 1.0 && p->omega < 2.0)) return CULGT_ERR_ARG;
     if (p->or_variant != 0 && p->or_variant != 1) return CULGT_ERR_ARG;
-    if (p->precision < CULGT_FP64 || p->precision > CULGT_MIXED) return CULGT_ERR_ARG;
+    if (p->precision < CULGT_FP64 || p->precision > CULGT_DF) return CULGT_ERR_ARG;
     if (p->nc == 3 && p->storage_reals != 0 && p->storage_reals != 12 && p->storage_reals != 18) return CULGT_ERR_NC;
     if (p->nc == 2 && p->storage_reals != 0 && p->storage_reals != 4) return CULGT_ERR_NC;
     if (!(p->theta_target >= 0.0) || std::isinf(p->theta_target)) return CULGT_ERR_ARG;
     if (p->max_sweeps < 0 || p->check_every < 1 || p->reunit_every < 0) return CULGT_ERR_ARG;
-    if (p->precision == CULGT_MIXED && !(p->switch_theta > 0.0)) return CULGT_ERR_ARG;
+    if ((p->precision == CULGT_MIXED || p->precision == CULGT_MIXED_DF) && !(p->switch_theta > 0.0))
+        return CULGT_ERR_ARG;
     if (p->dtype_in != 0 && p->dtype_in != 1) return CULGT_ERR_ARG;
+    if (p->threads_per_site < 0 || p->threads_per_site > 2) return CULGT_ERR_ARG;
+    if (p->block_size != 0 && p->block_size != 64 && p->block_size != 128 && p->block_size != 256) return CULGT_ERR_ARG;
     return CULGT_OK;
 }
 
@@ -76,13 +83,19 @@ size_t buffer_bytes(const Ops *o, const Geom &g) { return (size_t)8 * o->nchunk 
 void pick_ops(const culgt_params *p, const Ops **o32, const Ops **o64)
 {
     *o32 = *o64 = nullptr;
-    if (p->precision == CULGT_FP64) {
-        *o64 = get_ops(p->nc, 0, p->storage_reals ? p->storage_reals : default_storage(p->nc, 0));
-    } else if (p->precision == CULGT_FP32) {
-        *o32 = get_ops(p->nc, 1, p->storage_reals ? p->storage_reals : default_storage(p->nc, 1));
-    } else {
-        *o32 = get_ops(p->nc, 1, p->storage_reals ? p->storage_reals : default_storage(p->nc, 1));
+    const int sr32 = p->storage_reals ? p->storage_reals : default_storage(p->nc, 1);
+    switch (p->precision) {
+    case CULGT_FP64: *o64 = get_ops(p->nc, 0, p->storage_reals ? p->storage_reals : default_storage(p->nc, 0)); break;
+    case CULGT_FP32: *o32 = get_ops(p->nc, 1, sr32); break;
+    case CULGT_MIXED:
+        *o32 = get_ops(p->nc, 1, sr32);
         *o64 = get_ops(p->nc, 0, default_storage(p->nc, 0));
+        break;
+    case CULGT_MIXED_DF:
+        *o32 = get_ops(p->nc, 1, sr32);
+        *o64 = get_ops_df(p->nc);
+        break;
+    default: *o64 = get_ops_df(p->nc); break;
     }
 }
 
@@ -143,19 +156,106 @@ culgt_status unitarity_now(culgt_handle *h, double *err)
     return CULGT_OK;
 }
 
-// In the FP32 phase of a mixed handle the half-sweeps also accumulate g(x).
-void sweep_now(culgt_handle *h, int n)
+// Autotuner (the paper's runtime choice of kernel settings, Sec. 5): each
+// (threads per site, block size) mapping is timed on a scratch copy of the
+// links; the fastest is kept per (storage, lattice volume, accumulation) for
+// the process. All mappings give bitwise identical links, so the choice never
+// changes a result. Lattices below kTuneMinSites use the default mapping.
+constexpr int kTuneMinSites = 1 << 16;
+std::mutex g_tune_mutex;
+std::map<std::tuple<const Ops *, int, bool>, std::pair<int, int>> g_tune_cache;
+
+culgt_status autotune(culgt_handle *h, const Ops *o, void *buf, bool acc, int *tps_out, int *block_out)
 {
+    const culgt_params &p = h->prm;
+    int tps = p.threads_per_site ? p.threads_per_site : 1, block = p.block_size ? p.block_size : 128;
+    if ((p.threads_per_site && p.block_size) || h->geom.V < kTuneMinSites) {
+        *tps_out = tps;
+        *block_out = block;
+        return CULGT_OK;
+    }
+    auto key = std::make_tuple(o, h->geom.V, acc);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *tps_out = p.threads_per_site ? p.threads_per_site : it->second.first;
+            *block_out = p.block_size ? p.block_size : it->second.second;
+            return CULGT_OK;
+        }
+    }
+    size_t bytes = buffer_bytes(o, h->geom);
+    size_t gbytes = acc ? gauge_bytes(o, h->geom) : 0;
+    void *scratch = nullptr, *gscratch = nullptr;
+    if (cudaMalloc(&scratch, bytes + gbytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return CULGT_ERR_OOM;
+    }
+    if (acc) gscratch = (char *)scratch + bytes;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    CU(cudaMemcpyAsync(scratch, buf, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    if (acc) CU(cudaMemcpyAsync(gscratch, h->gacc, gbytes, cudaMemcpyDeviceToDevice, h->stream));
+    float best = 1e30f;
+    int best_tps = tps, best_block = block;
+    for (int t = 1; t <= 2; t++) {
+        if (p.threads_per_site && t != p.threads_per_site) continue;
+        for (int b : {64, 128, 256}) {
+            if (p.block_size && b != p.block_size) continue;
+            o->halfsweep(scratch, gscratch, h->geom, 0, p.omega, p.or_variant, t, b, h->stream);
+            cudaEventRecord(e0, h->stream);
+            for (int r = 0; r < 2; r++)
+                for (int parity = 0; parity < 2; parity++)
+                    o->halfsweep(scratch, gscratch, h->geom, parity, p.omega, p.or_variant, t, b, h->stream);
+            cudaEventRecord(e1, h->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            count_launch(-5);  // tuning launches are not part of the caller's work
+            if (ms < best) {
+                best = ms;
+                best_tps = t;
+                best_block = b;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(scratch);
+    CU(cudaGetLastError());
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = std::make_pair(best_tps, best_block);
+    }
+    *tps_out = best_tps;
+    *block_out = best_block;
+    return CULGT_OK;
+}
+
+culgt_status tuned_mapping(culgt_handle *h, int *tps, int *block)
+{
+    const bool acc = h->cur32 && h->gacc;
+    int &t = h->cur32 ? h->tps32 : h->tps64;
+    int &b = h->cur32 ? h->block32 : h->block64;
+    if (!t) ST(autotune(h, cur_ops(h), cur_buf(h), acc, &t, &b));
+    *tps = t;
+    *block = b;
+    return CULGT_OK;
+}
+
+// In the FP32 phase of a mixed handle the half-sweeps also accumulate g(x).
+culgt_status sweep_now(culgt_handle *h, int n)
+{
+    int tps, block;
+    ST(tuned_mapping(h, &tps, &block));
     const Ops *o = cur_ops(h);
     void *b = cur_buf(h);
-    const bool acc = h->cur32 && h->gacc;
+    void *acc = (h->cur32 && h->gacc) ? h->gacc : nullptr;
     for (int k = 0; k < n; k++)
-        for (int parity = 0; parity < 2; parity++) {
-            if (acc)
-                o->halfsweep_acc(b, h->gacc, h->geom, parity, h->prm.omega, h->prm.or_variant, h->stream);
-            else
-                o->halfsweep(b, h->geom, parity, h->prm.omega, h->prm.or_variant, h->stream);
-        }
+        for (int parity = 0; parity < 2; parity++)
+            o->halfsweep(b, acc, h->geom, parity, h->prm.omega, h->prm.or_variant, tps, block, h->stream);
+    return CULGT_OK;
 }
 
 void reunitarize_now(culgt_handle *h)
@@ -174,7 +274,7 @@ culgt_status run_phase(culgt_handle *h, double target, int *n, int *phase_sweeps
         int k = p.check_every;
         if (k > p.max_sweeps - *n) k = p.max_sweeps - *n;
         for (int j = 0; j < k; j++) {
-            sweep_now(h, 1);
+            ST(sweep_now(h, 1));
             ++*n;
             ++*phase_sweeps;
             if (p.reunit_every > 0 && *n % p.reunit_every == 0) reunitarize_now(h);
@@ -191,7 +291,7 @@ culgt_status fix_handle(culgt_handle *h, culgt_result *out)
     double theta = 0.0, F = 0.0;
     int n = 0;
     h->sweeps32 = h->sweeps64 = 0;
-    if (p.precision == CULGT_MIXED && h->cur32) {
+    if ((p.precision == CULGT_MIXED || p.precision == CULGT_MIXED_DF) && h->cur32) {
         ST(run_phase(h, p.switch_theta, &n, &h->sweeps32, &theta, &F));
         ST(culgt_handle_to_fp64(h));
     }
@@ -376,7 +476,7 @@ culgt_status culgt_store(culgt_handle *h, void *d_links)
 culgt_status culgt_handle_sweep(culgt_handle *h, int n_sweeps)
 {
     if (!h || !h->loaded || n_sweeps < 0) return CULGT_ERR_ARG;
-    sweep_now(h, n_sweeps);
+    ST(sweep_now(h, n_sweeps));
     CU(cudaGetLastError());
     return CULGT_OK;
 }
@@ -417,6 +517,12 @@ culgt_status culgt_handle_to_fp64(culgt_handle *h)
     CU(cudaGetLastError());
     h->cur32 = 0;
     return CULGT_OK;
+}
+
+culgt_status culgt_handle_tuning(culgt_handle *h, int *threads_per_site, int *block_size)
+{
+    if (!h || !h->loaded || !threads_per_site || !block_size) return CULGT_ERR_ARG;
+    return tuned_mapping(h, threads_per_site, block_size);
 }
 
 culgt_status culgt_handle_fix(culgt_handle *h, culgt_result *out)

@@ -79,7 +79,9 @@ struct Engine {
     culgt_status init(const culgt_params *p)
     {
         cp = *p;
-        has32 = p->precision != CULGT_FP64;
+        const bool mixed = p->precision == CULGT_MIXED || p->precision == CULGT_MIXED_DF;
+        const bool df = p->precision == CULGT_MIXED_DF || p->precision == CULGT_DF;
+        has32 = p->precision == CULGT_FP32 || mixed;
         has64 = p->precision != CULGT_FP32;
         int def32 = p->nc == 2 ? 4 : 12, def64 = p->nc == 2 ? 4 : 18;
         if (has32) {
@@ -87,7 +89,10 @@ struct Engine {
             o32 = get_ops(p->nc, 1, sr);
             b32 = get_bops(p->nc, 1, sr);
         }
-        if (has64) {
+        if (has64 && df) {
+            o64 = get_ops_df(p->nc);
+            b64 = get_bops_df(p->nc);
+        } else if (has64) {
             int sr = (p->precision == CULGT_FP64 && p->storage_reals) ? p->storage_reals : def64;
             o64 = get_ops(p->nc, 0, sr);
             b64 = get_bops(p->nc, 0, sr);
@@ -97,8 +102,8 @@ struct Engine {
         acc32 = has32 && (has64 || coulomb);
         acc64 = has64 && coulomb;
         rule.theta_target = p->theta_target;
-        rule.fp32_target = p->precision == CULGT_MIXED ? p->switch_theta : p->theta_target;
-        rule.fp32_next = p->precision == CULGT_MIXED ? PH_SWITCH : PH_DONE;
+        rule.fp32_target = mixed ? p->switch_theta : p->theta_target;
+        rule.fp32_next = mixed ? PH_SWITCH : PH_DONE;
         rule.max_sweeps = p->max_sweeps;
         if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
             (void)cudaGetLastError();
@@ -459,7 +464,7 @@ extern "C" culgt_status culgt_coulomb_fix(void *d_links, const culgt_params *p, 
         // g(x) as [V][Nc][Nc] complex double in canonical site order
         const BPhaseOps *b = e.has64 ? e.b64 : e.b32;
         const void *acc = e.has64 ? L.gacc64 : L.gacc32;
-        launch_gauge_to_canonical(p->nc, b->fp32, acc, (double *)d_gauge, L.g, e.s);
+        launch_gauge_to_canonical(p->nc, b->fp32 ? 1 : (e.o64->df ? 2 : 0), acc, (double *)d_gauge, L.g, e.s);
         if (cudaGetLastError() != cudaSuccess) return CULGT_ERR_CUDA;
     }
     EST(e.store_all());

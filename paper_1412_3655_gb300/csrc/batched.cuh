@@ -49,9 +49,6 @@ struct BRule {
     int max_sweeps;
 };
 
-template <class PG> struct AccType { typedef typename PG::Link type; };
-template <> struct AccType<void> { typedef int type; };
-
 // site (cb, p) of a problem: the site update of Sec. 2 on its own links, and
 // for PG != void the accumulation gacc(x) <- g(x) gacc(x) in PG's storage
 template <class P, class PG>
@@ -122,7 +119,7 @@ template <class P>
 __global__ void __launch_bounds__(kThetaTile) k_b_theta(const BProb *probs, const int *tile_prob, int want_phase,
                                                         int only_switched, double2 *partials)
 {
-    typedef typename P::Real T;
+    typedef typename ThetaReal<typename P::Real>::type T;
     const int tile = blockIdx.x;
     const BProb &pr = probs[tile_prob[tile]];
     double th = 0.0, fs = 0.0;
@@ -141,10 +138,10 @@ __global__ void __launch_bounds__(kThetaTile) k_b_theta(const BProb *probs, cons
             for (int mu = 0; mu < 4; mu++) {
                 if (mu < pr.mu_first) continue;
                 M3<T> u;
-                P::load(base + plane_offset(g, p, mu, P::NCHUNK) + cb, g.stride, u);
+                load_as<P>(base + plane_offset(g, p, mu, P::NCHUNK) + cb, g.stride, u);
                 f += u.re[0][0] + u.re[1][1] + u.re[2][2];
                 m3_acc(M, u);
-                P::load(base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1), g.stride, u);
+                load_as<P>(base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1), g.stride, u);
 #pragma unroll
                 for (int a = 0; a < 3; a++)
 #pragma unroll
@@ -161,12 +158,12 @@ __global__ void __launch_bounds__(kThetaTile) k_b_theta(const BProb *probs, cons
             for (int mu = 0; mu < 4; mu++) {
                 if (mu < pr.mu_first) continue;
                 Q4<T> u;
-                P::load(base + plane_offset(g, p, mu, P::NCHUNK) + cb, g.stride, u);
+                load_as<P>(base + plane_offset(g, p, mu, P::NCHUNK) + cb, g.stride, u);
                 f += u.a[0];
                 v1 += u.a[1];
                 v2 += u.a[2];
                 v3 += u.a[3];
-                P::load(base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1), g.stride, u);
+                load_as<P>(base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1), g.stride, u);
                 v1 -= u.a[1];
                 v2 -= u.a[2];
                 v3 -= u.a[3];
@@ -197,28 +194,33 @@ __global__ void __launch_bounds__(kThetaTile) k_b_rotate(const BProb *probs, con
     typename P64::Chunk *base = (typename P64::Chunk *)pr.links64;
     int x[4];
     decode_site(g, cb, p, x);
-    typename P64::Link gx;
+    typename Link64<P64>::type gx;
     gauge_fp64<PG>(gb + (size_t)p * PG::NCHUNK * g.stride + cb, g.stride, gx);
 #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
         if (mu < pr.mu_first) continue;
         int cbf = cb_shift(g, x, mu, 1);
-        typename P64::Link u, gf;
+        typename Link64<P64>::type u, gf, r;
         gauge_fp64<PG>(gb + (size_t)(p ^ 1) * PG::NCHUNK * g.stride + cbf, g.stride, gf);
         typename P64::Chunk *up = base + plane_offset(g, p, mu, P64::NCHUNK) + cb;
-        P64::load(up, g.stride, u);
+        load_as<P64>(up, g.stride, u);
         if constexpr (P64::NC == 3) {
-            M3<double> t1, t2;
+            M3<double> t1;
             m3_mul(t1, gx, u);
-            m3_mul_adj(t2, t1, gf);
-            P64::store(up, g.stride, t2);
+            m3_mul_adj(r, t1, gf);
         } else {
-            P64::store(up, g.stride, q_mul_adj(q_mul(gx, u), gf));
+            r = q_mul_adj(q_mul(gx, u), gf);
         }
+        typename P64::Link out;
+        convert_link(r, out);
+        P64::store(up, g.stride, out);
     }
     if constexpr (!std::is_void<PG64>::value) {
-        if (pr.gacc64) PG64::store((typename PG64::Chunk *)pr.gacc64 + (size_t)p * PG64::NCHUNK * g.stride + cb,
-                                   g.stride, gx);
+        if (pr.gacc64) {
+            typename PG64::Link ga;
+            convert_link(gx, ga);
+            PG64::store((typename PG64::Chunk *)pr.gacc64 + (size_t)p * PG64::NCHUNK * g.stride + cb, g.stride, ga);
+        }
     }
 }
 

@@ -26,11 +26,14 @@ struct BPhaseOps {
 };
 
 const BPhaseOps *get_bops(int nc, int fp32, int nreal);
+const BPhaseOps *get_bops_df(int nc);
 
-extern const BPhaseOps bops_su3_f12, bops_su3_f18, bops_su3_d18, bops_su3_d12, bops_su2_f4, bops_su2_d4;
+extern const BPhaseOps bops_su3_f12, bops_su3_f18, bops_su3_d18, bops_su3_d12, bops_su2_f4, bops_su2_d4,
+    bops_su3_df18, bops_su2_df4;
 
-// an accumulator (internal layout) -> [V][Nc][Nc] complex double, canonical site order
-void launch_gauge_to_canonical(int nc, int fp32, const void *gacc, double *out, const Geom &g, cudaStream_t s);
+// an accumulator (internal layout) -> [V][Nc][Nc] complex double, canonical site order;
+// kind 0 = FP64, 1 = FP32, 2 = double-float accumulator
+void launch_gauge_to_canonical(int nc, int kind, const void *gacc, double *out, const Geom &g, cudaStream_t s);
 
 template <class PG> __global__ void __launch_bounds__(256) k_gauge_to_canonical(const typename PG::Chunk *gacc,
                                                                                double *out, Geom g)
@@ -55,8 +58,9 @@ template <class PG> __global__ void __launch_bounds__(256) k_gauge_to_canonical(
             o[2 * k + 1] = (double)u.im[k / 3][k % 3];
         }
     } else {
-        o[0] = u.a[0]; o[1] = u.a[3]; o[2] = u.a[2]; o[3] = u.a[1];
-        o[4] = -u.a[2]; o[5] = u.a[1]; o[6] = u.a[0]; o[7] = -u.a[3];
+        const double a0 = (double)u.a[0], a1 = (double)u.a[1], a2 = (double)u.a[2], a3 = (double)u.a[3];
+        o[0] = a0; o[1] = a3; o[2] = a2; o[3] = a1;
+        o[4] = -a2; o[5] = a1; o[6] = a0; o[7] = -a3;
     }
 }
 
@@ -69,6 +73,7 @@ template <class P> struct BImpl {
     typedef typename AccParam<P>::type PG;
     typedef Param<P::NC, float, P::NC == 3 ? 12 : 4> PG32;
     static constexpr bool kFP32 = sizeof(typename P::Real) == 4;
+    static constexpr bool kDF = std::is_same<typename P::Real, dfl>::value;
 
     static void sweep(const BProb *probs, const int *map, int ntiles, int colour, int phase, double omega,
                       int variant, bool acc, cudaStream_t s)

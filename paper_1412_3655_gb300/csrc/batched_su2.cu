@@ -17,10 +17,17 @@ const BPhaseOps *get_bops(int nc, int fp32, int nreal)
     return nullptr;
 }
 
-void launch_gauge_to_canonical(int nc, int fp32, const void *gacc, double *out, const Geom &g, cudaStream_t s)
+const BPhaseOps *get_bops_df(int nc) { return nc == 3 ? &bops_su3_df18 : &bops_su2_df4; }
+
+void launch_gauge_to_canonical(int nc, int kind, const void *gacc, double *out, const Geom &g, cudaStream_t s)
 {
     unsigned nb = (unsigned)((g.V + 255) / 256);
-    if (nc == 3 && fp32)
+    const bool fp32 = kind == 1;
+    if (nc == 3 && kind == 2)
+        k_gauge_to_canonical<Param<3, dfl, 12>><<<nb, 256, 0, s>>>((const float4 *)gacc, out, g);
+    else if (nc == 2 && kind == 2)
+        k_gauge_to_canonical<Param<2, dfl, 4>><<<nb, 256, 0, s>>>((const float4 *)gacc, out, g);
+    else if (nc == 3 && fp32)
         k_gauge_to_canonical<Param<3, float, 12>><<<nb, 256, 0, s>>>((const float4 *)gacc, out, g);
     else if (nc == 3)
         k_gauge_to_canonical<Param<3, double, 12>><<<nb, 256, 0, s>>>((const double2 *)gacc, out, g);

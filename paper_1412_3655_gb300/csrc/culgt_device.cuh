@@ -19,6 +19,8 @@
 
 #include <type_traits>
 
+#include "dfloat.cuh"
+
 namespace culgt {
 
 struct Geom {
@@ -558,5 +560,85 @@ template <> struct Param<2, float, 4> {
         p[0] = make_float4(u.a[0], u.a[1], u.a[2], u.a[3]);
     }
 };
+
+// SU(3), double-float: one float4 (re.hi, re.lo, im.hi, im.lo) per complex
+// element, NREAL/2 chunks; the same 144 (96) bytes per link as FP64 18 (12)
+template <int NR> struct ParamDF3 {
+    typedef dfl Real;
+    typedef float4 Chunk;
+    typedef M3<dfl> Link;
+    static constexpr int NC = 3, NREAL = NR, NCHUNK = NR / 2;
+    static __device__ __forceinline__ void load_raw(const Chunk *p, size_t s, Link &u)
+    {
+#pragma unroll
+        for (int k = 0; k < NR / 2; k++) {
+            float4 c = p[k * s];
+            u.re[k / 3][k % 3] = dfl(c.x, c.y);
+            u.im[k / 3][k % 3] = dfl(c.z, c.w);
+        }
+    }
+    static __device__ __forceinline__ void load(const Chunk *p, size_t s, Link &u)
+    {
+        load_raw(p, s, u);
+        if constexpr (NR == 12) m3_rebuild_row2(u);
+    }
+    static __device__ __forceinline__ void store(Chunk *p, size_t s, const Link &u)
+    {
+#pragma unroll
+        for (int k = 0; k < NR / 2; k++)
+            p[k * s] = make_float4(u.re[k / 3][k % 3].hi, u.re[k / 3][k % 3].lo, u.im[k / 3][k % 3].hi,
+                                   u.im[k / 3][k % 3].lo);
+    }
+};
+template <> struct Param<3, dfl, 18> : ParamDF3<18> {};
+template <> struct Param<3, dfl, 12> : ParamDF3<12> {};
+
+// SU(2), double-float quaternion: 2 x float4 = (a0, a1), (a2, a3)
+template <> struct Param<2, dfl, 4> {
+    typedef dfl Real;
+    typedef float4 Chunk;
+    typedef Q4<dfl> Link;
+    static constexpr int NC = 2, NREAL = 4, NCHUNK = 2;
+    static __device__ __forceinline__ void load(const Chunk *p, size_t s, Link &u)
+    {
+        float4 c0 = p[0], c1 = p[s];
+        u.a[0] = dfl(c0.x, c0.y); u.a[1] = dfl(c0.z, c0.w);
+        u.a[2] = dfl(c1.x, c1.y); u.a[3] = dfl(c1.z, c1.w);
+    }
+    static __device__ __forceinline__ void load_raw(const Chunk *p, size_t s, Link &u) { load(p, s, u); }
+    static __device__ __forceinline__ void store(Chunk *p, size_t s, const Link &u)
+    {
+        p[0] = make_float4(u.a[0].hi, u.a[0].lo, u.a[1].hi, u.a[1].lo);
+        p[s] = make_float4(u.a[2].hi, u.a[2].lo, u.a[3].hi, u.a[3].lo);
+    }
+};
+
+// arithmetic type of the theta / F reduction for a storage type: FP32 links
+// in FP32 (per site), FP64 and double-float links in FP64
+template <typename R> struct ThetaReal { typedef R type; };
+template <> struct ThetaReal<dfl> { typedef double type; };
+
+template <class P, typename T>
+__device__ __forceinline__ void load_as(const typename P::Chunk *p, size_t s, M3<T> &u)
+{
+    typename P::Link a;
+    P::load(p, s, a);
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            u.re[i][j] = (T)a.re[i][j];
+            u.im[i][j] = (T)a.im[i][j];
+        }
+}
+
+template <class P, typename T>
+__device__ __forceinline__ void load_as(const typename P::Chunk *p, size_t s, Q4<T> &u)
+{
+    typename P::Link a;
+    P::load(p, s, a);
+#pragma unroll
+    for (int k = 0; k < 4; k++) u.a[k] = (T)a.a[k];
+}
 
 } // namespace culgt

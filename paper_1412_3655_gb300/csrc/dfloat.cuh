@@ -1,0 +1,132 @@
+// Double-float ("float-float") numbers: x = hi + lo with two floats,
+// |lo| <= ulp(hi)/2, about 48 significant bits (unit roundoff 2^-48 ~ 3.6e-15
+// against FP64's 2^-53). Built from error-free transformations (Knuth's
+// two-sum, Dekker's fast two-sum, the FMA-based exact product), so all of the
+// arithmetic runs on the FP32 pipes. GB300 executes FP32 at 59 times its FP64
+// rate, which makes this the fast way to FP64-class precision there.
+//
+// The type provides what the templated SU(3)/SU(2) algebra uses: + - *,
+// fma, rsqrt, sqrt, division, comparison, and conversion to and from double.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace culgt {
+
+// the double-float overloads below live in this namespace; keep the float and
+// double ones visible next to them for unqualified calls in templates
+using ::atan2;
+using ::cos;
+using ::fma;
+using ::rsqrt;
+using ::sin;
+using ::sqrt;
+
+struct dfl {
+    float hi, lo;
+    __host__ __device__ constexpr dfl() : hi(0.0f), lo(0.0f) {}
+    __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ constexpr dfl(int i) : hi((float)i), lo(0.0f) {}
+    __host__ __device__ constexpr dfl(float f) : hi(f), lo(0.0f) {}
+    // nearest float, then the float nearest the remainder
+    __host__ __device__ constexpr dfl(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+    __host__ __device__ explicit operator float() const { return hi + lo; }
+};
+
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// s + e = a + b exactly when |a| >= |b| (Dekker)
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    e = b - (s - a);
+}
+
+__device__ __forceinline__ dfl operator+(dfl a, dfl b)
+{
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e += a.lo + b.lo;
+    dfl r;
+    fast_two_sum(s, e, r.hi, r.lo);
+    return r;
+}
+
+__device__ __forceinline__ dfl operator-(dfl a) { return dfl(-a.hi, -a.lo); }
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
+
+__device__ __forceinline__ dfl operator*(dfl a, dfl b)
+{
+    float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);  // exact error of the leading product
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    dfl r;
+    fast_two_sum(p, e, r.hi, r.lo);
+    return r;
+}
+
+// a b + c with one normalisation
+__device__ __forceinline__ dfl fma(dfl a, dfl b, dfl c)
+{
+    float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    float s, t;
+    two_sum(p, c.hi, s, t);
+    t += e + c.lo;
+    dfl r;
+    fast_two_sum(s, t, r.hi, r.lo);
+    return r;
+}
+
+__device__ __forceinline__ dfl &operator+=(dfl &a, dfl b) { return a = a + b; }
+__device__ __forceinline__ dfl &operator-=(dfl &a, dfl b) { return a = a - b; }
+__device__ __forceinline__ dfl &operator*=(dfl &a, dfl b) { return a = a * b; }
+
+__device__ __forceinline__ bool operator>(dfl a, dfl b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__device__ __forceinline__ bool operator<(dfl a, dfl b) { return b > a; }
+
+// 1/sqrt(x): the float estimate refined by one Newton step in double-float,
+// r' = r + r (1 - x r^2) / 2; the correction is small, so it needs only float
+// precision in its product
+__device__ __forceinline__ dfl rsqrt(dfl x)
+{
+    float r = rsqrtf(x.hi);
+    dfl rr = dfl(r) * dfl(r);
+    dfl y = x * rr;
+    dfl e = dfl(1.0f) - y;
+    float c = 0.5f * r * e.hi;
+    dfl out;
+    fast_two_sum(r, c, out.hi, out.lo);
+    return out;
+}
+
+__device__ __forceinline__ dfl sqrt(dfl x) { return x.hi > 0.0f ? x * rsqrt(x) : dfl(0.0f); }
+
+// 1/b by one Newton step from the float reciprocal, then a/b = a (1/b)
+__device__ __forceinline__ dfl operator/(dfl a, dfl b)
+{
+    float r = 1.0f / b.hi;
+    dfl e = dfl(1.0f) - b * dfl(r);
+    float c = r * e.hi;
+    dfl inv;
+    fast_two_sum(r, c, inv.hi, inv.lo);
+    return a * inv;
+}
+
+// transcendental functions only appear in the exact-power overrelaxation
+// variant; they go through double
+__device__ __forceinline__ dfl atan2(dfl y, dfl x) { return dfl(::atan2((double)y, (double)x)); }
+__device__ __forceinline__ dfl sin(dfl x) { return dfl(::sin((double)x)); }
+__device__ __forceinline__ dfl cos(dfl x) { return dfl(::cos((double)x)); }
+
+} // namespace culgt

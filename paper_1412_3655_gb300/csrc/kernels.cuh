@@ -41,127 +41,199 @@ __device__ __forceinline__ void apply_right_adj(M3<typename P::Real> &t, const M
     if constexpr (P::NREAL == 18) m3_rebuild_row2(t);
 }
 
+// swap a value with the partner lane (lane ^ 1)
+__device__ __forceinline__ float shfl_pair(float v) { return __shfl_xor_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_pair(double v) { return __shfl_xor_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ dfl shfl_pair(dfl v) { return dfl(shfl_pair(v.hi), shfl_pair(v.lo)); }
+
+// The eight links of a site split into two halves, mu in {0,1} and {2,3};
+// K is summed per half (forward link, then backward link, mu ascending) and
+// then K = K_half0 + K_half1. One thread per site and a pair of threads per
+// site (each holding one half, exchanging its partial K with a shuffle) thus
+// form K, g and the new links bitwise alike.
+//
+// TPS = 1: this thread does the whole site (half ignored).
+// TPS = 2: this thread does the links of `half`; both lanes of a pair must
+// reach the shuffles, so an out-of-range pair passes valid = false instead
+// of returning.
+template <class P, bool KEEP, int TPS>
+__device__ __forceinline__ void su3_update(typename P::Chunk *base, const Geom &g, int cb, int p, int half, bool valid,
+                                           int mu_first, typename P::Real omega, int variant,
+                                           M3<typename P::Real> *gout)
+{
+    typedef typename P::Real T;
+    typedef typename P::Chunk C;
+    constexpr int NMU = 4 / TPS;
+    const int mu0 = TPS == 1 ? 0 : 2 * half;
+    int x[4];
+    decode_site(g, valid ? cb : 0, p, x);
+    C *fwd[NMU];
+    C *bwd[NMU];
+#pragma unroll
+    for (int k = 0; k < NMU; k++) {
+        const int mu = mu0 + k;
+        fwd[k] = base + plane_offset(g, p, mu, P::NCHUNK) + cb;
+        bwd[k] = base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1);
+    }
+    // Ka: this thread's half (TPS = 2) or mu in {0,1} (TPS = 1); Kb: mu in {2,3} (TPS = 1)
+    M3<T> Ka, Kb;
+    m3_zero(Ka);
+    m3_zero(Kb);
+    M3<T> uf[KEEP ? NMU : 1], ub[KEEP ? NMU : 1];
+#pragma unroll
+    for (int k = 0; k < NMU; k++) {
+        const int mu = mu0 + k;
+        if (mu < mu_first || !valid) continue;
+        M3<T> &f = uf[KEEP ? k : 0];
+        M3<T> &b = ub[KEEP ? k : 0];
+        M3<T> &Kt = (TPS == 1 && k >= 2) ? Kb : Ka;
+        P::load(fwd[k], g.stride, f);
+        P::load(bwd[k], g.stride, b);
+        m3_acc(Kt, f);
+        m3_acc_adj(Kt, b);
+    }
+    M3<T> K;
+    if constexpr (TPS == 1) {
+        K = Ka;
+        m3_acc(K, Kb);
+    } else {
+        // the partner's partial; both lanes then add half 0 + half 1
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                T orr = shfl_pair(Ka.re[i][j]), oi = shfl_pair(Ka.im[i][j]);
+                K.re[i][j] = half ? orr + Ka.re[i][j] : Ka.re[i][j] + orr;
+                K.im[i][j] = half ? oi + Ka.im[i][j] : Ka.im[i][j] + oi;
+            }
+    }
+    M3<T> G;
+    su3_local_gauge(K, G, omega, variant);
+#pragma unroll
+    for (int k = 0; k < NMU; k++) {
+        const int mu = mu0 + k;
+        if (mu < mu_first || !valid) continue;
+        M3<T> &f = uf[KEEP ? k : 0];
+        M3<T> &b = ub[KEEP ? k : 0];
+        M3<T> t;
+        if (!KEEP) P::load(fwd[k], g.stride, f);
+        apply_left<P>(t, G, f);
+        P::store(fwd[k], g.stride, t);
+        if (!KEEP) P::load(bwd[k], g.stride, b);
+        apply_right_adj<P>(t, b, G);
+        P::store(bwd[k], g.stride, t);
+    }
+    if (gout) *gout = G;
+}
+
+template <class P, int TPS>
+__device__ __forceinline__ void su2_update(typename P::Chunk *base, const Geom &g, int cb, int p, int half, bool valid,
+                                           int mu_first, typename P::Real omega, int variant,
+                                           Q4<typename P::Real> *gout)
+{
+    typedef typename P::Real T;
+    typedef typename P::Chunk C;
+    constexpr int NMU = 4 / TPS;
+    const int mu0 = TPS == 1 ? 0 : 2 * half;
+    int x[4];
+    decode_site(g, valid ? cb : 0, p, x);
+    C *fwd[NMU];
+    C *bwd[NMU];
+    Q4<T> uf[NMU], ub[NMU];
+    Q4<T> Ka = {{T(0), T(0), T(0), T(0)}}, Kb = Ka;
+#pragma unroll
+    for (int k = 0; k < NMU; k++) {
+        const int mu = mu0 + k;
+        fwd[k] = base + plane_offset(g, p, mu, P::NCHUNK) + cb;
+        bwd[k] = base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1);
+        if (mu < mu_first || !valid) continue;
+        P::load(fwd[k], g.stride, uf[k]);
+        P::load(bwd[k], g.stride, ub[k]);
+        // U_f + U_b^+ : (f0 + b0, f - b)
+        Q4<T> &h = (TPS == 1 && k >= 2) ? Kb : Ka;
+        h.a[0] += uf[k].a[0] + ub[k].a[0];
+        h.a[1] += uf[k].a[1] - ub[k].a[1];
+        h.a[2] += uf[k].a[2] - ub[k].a[2];
+        h.a[3] += uf[k].a[3] - ub[k].a[3];
+    }
+    Q4<T> K;
+    if constexpr (TPS == 1) {
+#pragma unroll
+        for (int c = 0; c < 4; c++) K.a[c] = Ka.a[c] + Kb.a[c];
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            T o = shfl_pair(Ka.a[c]);
+            K.a[c] = half ? o + Ka.a[c] : Ka.a[c] + o;
+        }
+    }
+    Q4<T> G = su2_local_gauge(K, omega, variant);
+#pragma unroll
+    for (int k = 0; k < NMU; k++) {
+        const int mu = mu0 + k;
+        if (mu < mu_first || !valid) continue;
+        P::store(fwd[k], g.stride, q_mul(G, uf[k]));
+        P::store(bwd[k], g.stride, q_mul_adj(ub[k], G));
+    }
+    if (gout) *gout = G;
+}
+
+// one thread per site (the batched engine's mapping)
 template <class P, bool KEEP>
 __device__ __forceinline__ void su3_site_update(typename P::Chunk *base, const Geom &g, int cb, int p, int mu_first,
                                                 typename P::Real omega, int variant, M3<typename P::Real> *gout)
 {
-    typedef typename P::Real T;
-    typedef typename P::Chunk C;
-    int x[4];
-    decode_site(g, cb, p, x);
-    const int q = p ^ 1;
-    C *fwd[4];
-    C *bwd[4];
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-        fwd[mu] = base + plane_offset(g, p, mu, P::NCHUNK) + cb;
-        bwd[mu] = base + plane_offset(g, q, mu, P::NCHUNK) + cb_shift(g, x, mu, -1);
-    }
-    M3<T> K;
-    m3_zero(K);
-    if (KEEP) {
-        M3<T> uf[4], ub[4];
-#pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
-            if (mu < mu_first) continue;
-            P::load(fwd[mu], g.stride, uf[mu]);
-            P::load(bwd[mu], g.stride, ub[mu]);
-        }
-#pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
-            if (mu < mu_first) continue;
-            m3_acc(K, uf[mu]);
-            m3_acc_adj(K, ub[mu]);
-        }
-        M3<T> G;
-        su3_local_gauge(K, G, omega, variant);
-#pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
-            if (mu < mu_first) continue;
-            M3<T> t;
-            apply_left<P>(t, G, uf[mu]);
-            P::store(fwd[mu], g.stride, t);
-            apply_right_adj<P>(t, ub[mu], G);
-            P::store(bwd[mu], g.stride, t);
-        }
-        if (gout) *gout = G;
-    } else {
-#pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
-            if (mu < mu_first) continue;
-            M3<T> u;
-            P::load(fwd[mu], g.stride, u);
-            m3_acc(K, u);
-            P::load(bwd[mu], g.stride, u);
-            m3_acc_adj(K, u);
-        }
-        M3<T> G;
-        su3_local_gauge(K, G, omega, variant);
-#pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
-            if (mu < mu_first) continue;
-            M3<T> u, t;
-            P::load(fwd[mu], g.stride, u);
-            apply_left<P>(t, G, u);
-            P::store(fwd[mu], g.stride, t);
-            P::load(bwd[mu], g.stride, u);
-            apply_right_adj<P>(t, u, G);
-            P::store(bwd[mu], g.stride, t);
-        }
-        if (gout) *gout = G;
-    }
+    su3_update<P, KEEP, 1>(base, g, cb, p, 0, true, mu_first, omega, variant, gout);
 }
 
 template <class P>
 __device__ __forceinline__ void su2_site_update(typename P::Chunk *base, const Geom &g, int cb, int p, int mu_first,
                                                 typename P::Real omega, int variant, Q4<typename P::Real> *gout)
 {
-    typedef typename P::Real T;
-    typedef typename P::Chunk C;
-    int x[4];
-    decode_site(g, cb, p, x);
-    const int q = p ^ 1;
-    C *fwd[4];
-    C *bwd[4];
-    Q4<T> uf[4], ub[4];
-    Q4<T> K = {{T(0), T(0), T(0), T(0)}};
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-        fwd[mu] = base + plane_offset(g, p, mu, P::NCHUNK) + cb;
-        bwd[mu] = base + plane_offset(g, q, mu, P::NCHUNK) + cb_shift(g, x, mu, -1);
-        if (mu < mu_first) continue;
-        P::load(fwd[mu], g.stride, uf[mu]);
-        P::load(bwd[mu], g.stride, ub[mu]);
-    }
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-        if (mu < mu_first) continue;
-        // U_f + U_b^+ : (f0 + b0, f - b)
-        K.a[0] += uf[mu].a[0] + ub[mu].a[0];
-        K.a[1] += uf[mu].a[1] - ub[mu].a[1];
-        K.a[2] += uf[mu].a[2] - ub[mu].a[2];
-        K.a[3] += uf[mu].a[3] - ub[mu].a[3];
-    }
-    Q4<T> G = su2_local_gauge(K, omega, variant);
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-        if (mu < mu_first) continue;
-        P::store(fwd[mu], g.stride, q_mul(G, uf[mu]));
-        P::store(bwd[mu], g.stride, q_mul_adj(ub[mu], G));
-    }
-    if (gout) *gout = G;
+    su2_update<P, 1>(base, g, cb, p, 0, true, mu_first, omega, variant, gout);
 }
 
-template <class P>
-__global__ void __launch_bounds__(128) k_halfsweep(typename P::Chunk *base, Geom g, int parity, typename P::Real omega,
-                                                   int variant)
+// links held between gather and update with two threads per site
+template <class P> struct KeepLinks2 {
+    static constexpr bool value = (sizeof(typename P::Real) * P::NREAL * 4 <= 4 * 12 * 8);
+};
+
+// Half-sweep with TPS threads per site (thread t: site t / TPS, half t % TPS);
+// ACC: also accumulate gacc(x) <- g(x) gacc(x) (mixed FP32 phase)
+template <class P, int TPS, class PG>
+__global__ void __launch_bounds__(256) k_halfsweep_v(typename P::Chunk *base, typename PG::Chunk *gacc, Geom g,
+                                                     int parity, typename P::Real omega, int variant, int acc)
 {
-    int cb = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cb >= g.Vh) return;
-    if constexpr (P::NC == 3)
-        su3_site_update<P, KeepLinks<P>::value>(base, g, cb, parity, 0, omega, variant, nullptr);
-    else
-        su2_site_update<P>(base, g, cb, parity, 0, omega, variant, nullptr);
+    typedef typename P::Real T;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cb = t / TPS, half = t % TPS;
+    const bool valid = cb < g.Vh;
+    if (TPS == 1 && !valid) return;
+    if constexpr (P::NC == 3) {
+        constexpr bool KEEP = TPS == 1 ? KeepLinks<P>::value : KeepLinks2<P>::value;
+        M3<T> G;
+        su3_update<P, KEEP, TPS>(base, g, cb, parity, half, valid, 0, omega, variant, &G);
+        if constexpr (std::is_same<typename PG::Real, T>::value) {
+            if (acc && valid && half == 0) {
+                typename PG::Chunk *gp = gacc + (size_t)parity * PG::NCHUNK * g.stride + cb;
+                M3<T> a, b;
+                PG::load(gp, g.stride, a);
+                m3_mul_rows<0, 1>(b, G, a);
+                PG::store(gp, g.stride, b);
+            }
+        }
+    } else {
+        Q4<T> G;
+        su2_update<P, TPS>(base, g, cb, parity, half, valid, 0, omega, variant, &G);
+        if constexpr (std::is_same<typename PG::Real, T>::value) {
+            if (acc && valid && half == 0) {
+                typename PG::Chunk *gp = gacc + (size_t)parity * PG::NCHUNK * g.stride + cb;
+                Q4<T> a;
+                PG::load(gp, g.stride, a);
+                PG::store(gp, g.stride, q_mul(G, a));
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -227,7 +299,7 @@ __device__ __forceinline__ void block_reduce2(double a, double b, double2 *parti
 template <class P>
 __global__ void __launch_bounds__(256) k_theta(const typename P::Chunk *base, Geom g, int mu_first, double2 *partials)
 {
-    typedef typename P::Real T;
+    typedef typename ThetaReal<typename P::Real>::type T;
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     double th = 0.0, fs = 0.0;
     if (s < 2 * g.Vh) {
@@ -243,7 +315,7 @@ __global__ void __launch_bounds__(256) k_theta(const typename P::Chunk *base, Ge
             for (int mu = 0; mu < 4; mu++) {
                 if (mu < mu_first) continue;
                 M3<T> u;
-                P::load(base + plane_offset(g, p, mu, P::NCHUNK) + cb, g.stride, u);
+                load_as<P>(base + plane_offset(g, p, mu, P::NCHUNK) + cb, g.stride, u);
                 f += u.re[0][0] + u.re[1][1] + u.re[2][2];
 #pragma unroll
                 for (int a = 0; a < 3; a++)
@@ -252,7 +324,7 @@ __global__ void __launch_bounds__(256) k_theta(const typename P::Chunk *base, Ge
                         M.re[a][b] += u.re[a][b];
                         M.im[a][b] += u.im[a][b];
                     }
-                P::load(base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1), g.stride, u);
+                load_as<P>(base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1), g.stride, u);
 #pragma unroll
                 for (int a = 0; a < 3; a++)
 #pragma unroll
@@ -269,12 +341,12 @@ __global__ void __launch_bounds__(256) k_theta(const typename P::Chunk *base, Ge
             for (int mu = 0; mu < 4; mu++) {
                 if (mu < mu_first) continue;
                 Q4<T> u;
-                P::load(base + plane_offset(g, p, mu, P::NCHUNK) + cb, g.stride, u);
+                load_as<P>(base + plane_offset(g, p, mu, P::NCHUNK) + cb, g.stride, u);
                 f += u.a[0];
                 v1 += u.a[1];
                 v2 += u.a[2];
                 v3 += u.a[3];
-                P::load(base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1), g.stride, u);
+                load_as<P>(base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1), g.stride, u);
                 v1 -= u.a[1];
                 v2 -= u.a[2];
                 v3 -= u.a[3];
@@ -498,6 +570,28 @@ __global__ void __launch_bounds__(256) k_to_canonical(const typename P::Chunk *b
 // K5: precision switch FP32 -> FP64, one thread per (parity, mu, site): the
 // stored rows are widened and the link reunitarised in FP64 (row 2 rebuilt).
 
+template <typename T> __device__ __forceinline__ void convert_link(const M3<double> &a, M3<T> &b)
+{
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            b.re[i][j] = (T)a.re[i][j];
+            b.im[i][j] = (T)a.im[i][j];
+        }
+}
+
+template <typename T> __device__ __forceinline__ void convert_link(const Q4<double> &a, Q4<T> &b)
+{
+#pragma unroll
+    for (int k = 0; k < 4; k++) b.a[k] = (T)a.a[k];
+}
+
+// the FP64 form of a link type (M3<double> or Q4<double>)
+template <class P> struct Link64 {
+    typedef typename std::conditional<P::NC == 3, M3<double>, Q4<double>>::type type;
+};
+
 template <class PIn, class POut>
 __global__ void __launch_bounds__(256) k_widen(const typename PIn::Chunk *src, typename POut::Chunk *dst, Geom g)
 {
@@ -507,7 +601,7 @@ __global__ void __launch_bounds__(256) k_widen(const typename PIn::Chunk *src, t
     int cb = (int)(t - (long long)plane * g.Vh);
     typename PIn::Link a;
     PIn::load_raw(src + (size_t)plane * PIn::NCHUNK * g.stride + cb, g.stride, a);
-    typename POut::Link b;
+    typename Link64<PIn>::type b;
     if constexpr (PIn::NC == 3) {
 #pragma unroll
         for (int r = 0; r < 2; r++)
@@ -528,7 +622,9 @@ __global__ void __launch_bounds__(256) k_widen(const typename PIn::Chunk *src, t
 #pragma unroll
         for (int k = 0; k < 4; k++) b.a[k] *= n;
     }
-    POut::store(dst + (size_t)plane * POut::NCHUNK * g.stride + cb, g.stride, b);
+    typename POut::Link c;
+    convert_link(b, c);
+    POut::store(dst + (size_t)plane * POut::NCHUNK * g.stride + cb, g.stride, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -543,28 +639,6 @@ template <class PG> __device__ __forceinline__ typename PG::Chunk *gauge_ptr(typ
                                                                              int p, int cb)
 {
     return gb + (size_t)p * PG::NCHUNK * g.stride + cb;
-}
-
-template <class P, class PG>
-__global__ void __launch_bounds__(128) k_halfsweep_acc(typename P::Chunk *base, typename PG::Chunk *gbase, Geom g,
-                                                       int parity, typename P::Real omega, int variant)
-{
-    typedef typename P::Real T;
-    int cb = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cb >= g.Vh) return;
-    typename PG::Chunk *gp = gauge_ptr<PG>(gbase, g, parity, cb);
-    if constexpr (P::NC == 3) {
-        M3<T> G, A, B;
-        su3_site_update<P, KeepLinks<P>::value>(base, g, cb, parity, 0, omega, variant, &G);
-        PG::load(gp, g.stride, A);
-        m3_mul(B, G, A);
-        PG::store(gp, g.stride, B);
-    } else {
-        Q4<T> G, A;
-        su2_site_update<P>(base, g, cb, parity, 0, omega, variant, &G);
-        PG::load(gp, g.stride, A);
-        PG::store(gp, g.stride, q_mul(G, A));
-    }
 }
 
 template <class PG> __global__ void __launch_bounds__(256) k_gauge_identity(typename PG::Chunk *gbase, Geom g)
@@ -582,8 +656,7 @@ template <class PG> __global__ void __launch_bounds__(256) k_gauge_identity(type
 }
 
 // g(x) in FP64, reunitarised, from the FP32 accumulator
-template <class PG, typename L>
-__device__ __forceinline__ void gauge_fp64(const typename PG::Chunk *p, size_t s, L &out)
+template <class PG, typename L> __device__ __forceinline__ void gauge_fp64(const typename PG::Chunk *p, size_t s, L &out)
 {
     typename PG::Link a;
     PG::load_raw(p, s, a);
@@ -623,18 +696,20 @@ __global__ void __launch_bounds__(128) k_rotate_orbit(const typename PG::Chunk *
     decode_site(g, cb, p, x);
     int cbf = cb_shift(g, x, mu, 1);
     typename P64::Chunk *up = base + plane_offset(g, p, mu, P64::NCHUNK) + cb;
-    typename P64::Link u, gx, gf;
-    P64::load(up, g.stride, u);
+    typename Link64<P64>::type u, gx, gf, r;
+    load_as<P64>(up, g.stride, u);
     gauge_fp64<PG>(gbase + (size_t)p * PG::NCHUNK * g.stride + cb, g.stride, gx);
     gauge_fp64<PG>(gbase + (size_t)(p ^ 1) * PG::NCHUNK * g.stride + cbf, g.stride, gf);
     if constexpr (P64::NC == 3) {
-        M3<double> t1, t2;
+        M3<double> t1;
         m3_mul(t1, gx, u);
-        m3_mul_adj(t2, t1, gf);
-        P64::store(up, g.stride, t2);
+        m3_mul_adj(r, t1, gf);
     } else {
-        P64::store(up, g.stride, q_mul_adj(q_mul(gx, u), gf));
+        r = q_mul_adj(q_mul(gx, u), gf);
     }
+    typename P64::Link out;
+    convert_link(r, out);
+    P64::store(up, g.stride, out);
 }
 
 } // namespace culgt

@@ -24,18 +24,19 @@ struct Ops {
     int nc;         // 2 or 3
     int nreal;      // reals per link in device memory
     int fp32;       // 1 if the links are float
+    int df;         // 1 if the links are double-float pairs
     int nchunk;     // chunks per link
     int chunk_bytes;
-    // one checkerboard half-sweep of the given parity (mu_first 0: Landau)
-    void (*halfsweep)(void *base, const Geom &g, int parity, double omega, int variant, cudaStream_t s);
+    // one checkerboard half-sweep of the given parity, tps (1 or 2) threads per
+    // site in blocks of `block` threads; gacc != null (FP32 storage) also
+    // accumulates g(x) per site. Every (tps, block) gives the same result.
+    void (*halfsweep)(void *base, void *gacc, const Geom &g, int parity, double omega, int variant, int tps,
+                      int block, cudaStream_t s);
     // per-block partial sums of (tr Delta Delta^+, sum Re tr U) over all sites; returns the block count
     int (*theta_partials)(const void *base, const Geom &g, int mu_first, double2 *partials, cudaStream_t s);
     // per-block partial sums of the plaquette trace; returns the block count
     int (*plaq_partials)(const void *base, const Geom &g, double2 *partials, cudaStream_t s);
     void (*reunitarize)(void *base, const Geom &g, cudaStream_t s);
-    // half-sweep that also accumulates gacc(x) <- g(x) gacc(x) (FP32 storage only)
-    void (*halfsweep_acc)(void *base, void *gacc, const Geom &g, int parity, double omega, int variant,
-                          cudaStream_t s);
     void (*gauge_identity)(void *gacc, const Geom &g, cudaStream_t s);
     void (*gauge_reunitarize)(void *gacc, const Geom &g, cudaStream_t s);
     int gauge_nchunk;     // chunks per site of the FP32 accumulator (0 for FP64 storage)
@@ -71,6 +72,10 @@ void launch_finalize_max(const double2 *partials, int n, double *out, cudaStream
 // out[0] = sx * sum_k partials[k].x, out[1] = sy * sum_k partials[k].y, fixed order
 void launch_finalize2(const double2 *partials, int n, double sx, double sy, double *out, cudaStream_t s);
 
-extern const Ops ops_su3_d18, ops_su3_d12, ops_su3_f12, ops_su3_f18, ops_su2_d4, ops_su2_f4;
+extern const Ops ops_su3_d18, ops_su3_d12, ops_su3_f12, ops_su3_f18, ops_su2_d4, ops_su2_f4, ops_su3_df18,
+    ops_su2_df4;
+
+// double-float storage (18 reals for SU(3), quaternion for SU(2))
+const Ops *get_ops_df(int nc);
 
 } // namespace culgt

@@ -15,14 +15,24 @@ template <class P> struct GaugeParam {
 
 template <class P> struct OpsImpl {
     typedef typename P::Chunk C;
-    static constexpr int kSweepThreads = 128;
     static constexpr int kThetaThreads = 256;
     static constexpr int kPlaqThreads = 128;
 
-    static void halfsweep(void *base, const Geom &g, int parity, double omega, int variant, cudaStream_t s)
+    // tps threads per site, block threads per block; gacc != null also
+    // accumulates g (FP32 storage)
+    static void halfsweep(void *base, void *gacc, const Geom &g, int parity, double omega, int variant, int tps,
+                          int block, cudaStream_t s)
     {
-        k_halfsweep<P><<<blocks_for(g.Vh, kSweepThreads), kSweepThreads, 0, s>>>(
-            (C *)base, g, parity, (typename P::Real)omega, variant);
+        typedef typename GaugeParam<P>::type PG;
+        typedef typename PG::Chunk GC;
+        const typename P::Real w = (typename P::Real)omega;
+        const int acc = gacc != nullptr;
+        if (tps == 2)
+            k_halfsweep_v<P, 2, PG><<<blocks_for(2LL * g.Vh, block), block, 0, s>>>((C *)base, (GC *)gacc, g, parity,
+                                                                                   w, variant, acc);
+        else
+            k_halfsweep_v<P, 1, PG><<<blocks_for(g.Vh, block), block, 0, s>>>((C *)base, (GC *)gacc, g, parity, w,
+                                                                              variant, acc);
         count_launch();
     }
     static int theta_partials(const void *base, const Geom &g, int mu_first, double2 *partials, cudaStream_t s)
@@ -46,15 +56,6 @@ template <class P> struct OpsImpl {
     }
     typedef typename GaugeParam<P>::type PG;
     static constexpr bool kFP32 = sizeof(typename P::Real) == 4;
-    static void halfsweep_acc(void *base, void *gacc, const Geom &g, int parity, double omega, int variant,
-                              cudaStream_t s)
-    {
-        if constexpr (kFP32) {
-            k_halfsweep_acc<P, PG><<<blocks_for(g.Vh, kSweepThreads), kSweepThreads, 0, s>>>(
-                (C *)base, (typename PG::Chunk *)gacc, g, parity, (typename P::Real)omega, variant);
-            count_launch();
-        }
-    }
     static void gauge_identity(void *gacc, const Geom &g, cudaStream_t s)
     {
         k_gauge_identity<PG><<<blocks_for(2LL * g.Vh, 256), 256, 0, s>>>((typename PG::Chunk *)gacc, g);
@@ -98,13 +99,13 @@ template <class P> struct OpsImpl {
         o.nc = P::NC;
         o.nreal = P::NREAL;
         o.fp32 = sizeof(typename P::Real) == 4;
+        o.df = std::is_same<typename P::Real, dfl>::value;
         o.nchunk = P::NCHUNK;
         o.chunk_bytes = (int)sizeof(C);
         o.halfsweep = halfsweep;
         o.theta_partials = theta_partials;
         o.plaq_partials = plaq_partials;
         o.reunitarize = reunitarize;
-        o.halfsweep_acc = kFP32 ? halfsweep_acc : nullptr;
         o.gauge_identity = kFP32 ? gauge_identity : nullptr;
         o.gauge_reunitarize = kFP32 ? gauge_reunitarize : nullptr;
         o.gauge_nchunk = kFP32 ? PG::NCHUNK : 0;

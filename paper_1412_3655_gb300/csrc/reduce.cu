@@ -80,6 +80,8 @@ int max_partials(const Geom &g)
     return (int)(a > b ? a : b);
 }
 
+const Ops *get_ops_df(int nc) { return nc == 3 ? &ops_su3_df18 : &ops_su2_df4; }
+
 const Ops *get_ops(int nc, int fp32, int nreal)
 {
     if (nc == 3 && !fp32 && nreal == 18) return &ops_su3_d18;

@@ -20,7 +20,7 @@ LIBRARY_PATH = os.path.join(_HERE, "libculgt.so")
 OK, NOT_CONVERGED = 0, 1
 ERR_ARG, ERR_DIMS, ERR_NC, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_TIMEOUT = -1, -2, -3, -4, -5, -6, -7
 ERR_TOO_LARGE = -8
-FP64, FP32, MIXED = 0, 1, 2
+FP64, FP32, MIXED, MIXED_DF, DF = 0, 1, 2, 3, 4
 
 
 class CulgtError(RuntimeError):
@@ -43,6 +43,8 @@ class _Params(ctypes.Structure):
         ("reunit_every", ctypes.c_int),
         ("switch_theta", ctypes.c_double),
         ("dtype_in", ctypes.c_int),
+        ("threads_per_site", ctypes.c_int),
+        ("block_size", ctypes.c_int),
     ]
 
 
@@ -78,6 +80,8 @@ class Params:
     reunit_every: int = 100
     switch_theta: float = 1e-8
     dtype_in: int = 0
+    threads_per_site: int = 0
+    block_size: int = 0
 
     @classmethod
     def defaults(cls, nc, dims, **kw):
@@ -139,6 +143,7 @@ def library():
         "culgt_handle_reunitarize": (ip, [H]),
         "culgt_handle_to_fp64": (ip, [H]),
         "culgt_handle_fix": (ip, [H, R]),
+        "culgt_handle_tuning": (ip, [H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "culgt_landau_fix": (ip, [vp, P, vp, R]),
         "culgt_landau_fix_host": (ip, [vp, P, vp, R]),
         "culgt_sweep": (ip, [vp, P, ip, vp]),
@@ -357,6 +362,11 @@ class Handle:
 
     def culgt_handle_to_fp64(self):
         _check(library().culgt_handle_to_fp64(self._h), "culgt_handle_to_fp64")
+
+    def culgt_handle_tuning(self):
+        t, b = ctypes.c_int(), ctypes.c_int()
+        _check(library().culgt_handle_tuning(self._h, ctypes.byref(t), ctypes.byref(b)), "culgt_handle_tuning")
+        return t.value, b.value
 
     def culgt_handle_fix(self) -> Result:
         r = _Result()

@@ -59,8 +59,9 @@ def test_defaults_validate(lib):
     ({"omega": float("nan")}, -1),
     ({"check_every": 0}, -1),
     ({"max_sweeps": -1}, -1),
-    ({"precision": 3}, -1),
+    ({"precision": 5}, -1),
     ({"precision": 2, "switch_theta": 0.0}, -1),
+    ({"precision": 3, "switch_theta": -1.0}, -1),
     ({"theta_target": float("inf")}, -1),
     ({"dtype_in": 2}, -1),
     ({"or_variant": 2}, -1),
@@ -73,6 +74,14 @@ def test_validate_rejects(lib, change, code):
     # the one-call entry points check before touching the device
     so = lib.library()
     assert so.culgt_landau_fix(ctypes.c_void_p(16), ctypes.byref(p._c()), None, None) == code
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("nc", [2, 3])
+def test_every_precision_validates(lib, precision, nc):
+    p = lib.Params.defaults(nc, (4, 2, 4, 6), precision=precision)
+    assert lib.culgt_validate(p) == lib.OK
+    assert lib.culgt_workspace_bytes(p) > 0
 
 
 def test_null_pointers_rejected(lib):

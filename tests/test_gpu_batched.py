@@ -74,12 +74,14 @@ def test_coulomb_slices_retire_on_their_own(cu, orc, nc):
         assert res[t].F == pytest.approx(rr["F"][t], rel=1e-10)
 
 
+@pytest.mark.parametrize("precision", ["mixed", "mixed_df"])
 @pytest.mark.parametrize("nc", [2, 3])
-def test_coulomb_mixed(cu, orc, nc):
+def test_coulomb_mixed(cu, orc, nc, precision):
     dims = (4, 4, 4, 2)
     U = synth.gauge_config(dims, nc, 0.3, 5)
     d = to_dev(U)
-    p = cu.Params.defaults(nc, dims, precision=cu.MIXED, check_every=5, reunit_every=50, max_sweeps=4000)
+    prec = cu.MIXED if precision == "mixed" else cu.MIXED_DF
+    p = cu.Params.defaults(nc, dims, precision=prec, check_every=5, reunit_every=50, max_sweeps=4000)
     res = cu.culgt_coulomb_fix(d, p)
     ref = U.copy()
     rr = orc.coulomb_fix(ref, dims, nc, 1.7, 1e-12, 4000, 1, 0)
@@ -94,11 +96,11 @@ def test_coulomb_mixed(cu, orc, nc):
         assert th < 1e-12
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_df"])
 @pytest.mark.parametrize("nc", [2, 3])
 def test_batched_uneven_lattices(cu, orc, nc, precision):
     """4^4, 2x4x6x4, 6^4 and two gauge copies of 4^4 in one batch."""
-    prec = cu.FP64 if precision == "fp64" else cu.MIXED
+    prec = {"fp64": cu.FP64, "mixed": cu.MIXED, "mixed_df": cu.MIXED_DF}[precision]
     cases = [((4, 4, 4, 4), 1, 0), ((2, 4, 6, 4), 2, 0), ((6, 6, 6, 6), 3, 0), ((4, 4, 4, 4), 1, 1),
              ((4, 4, 4, 4), 1, 2)]
     Us = [synth.gauge_config(dims, nc, 0.3, seed, copy=copy) for dims, seed, copy in cases]

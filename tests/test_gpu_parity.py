@@ -110,6 +110,40 @@ def test_one_sweep_fp32(cu, orc, dims, nc):
             assert_sweep_close(from_dev(d, U.shape), ref, 5e-6, good)
 
 
+@pytest.mark.parametrize("dims,nc", CASES)
+def test_one_sweep_double_float(cu, orc, dims, nc):
+    """Double-float sweeps (pairs of floats, unit roundoff 2^-48, 32 times
+    FP64's): one sweep within 32 x the FP64 bound, 3.2e-12."""
+    U0 = synth.gauge_config(dims, nc, 0.3, 2)
+    for U, good in [(U0, False), (warmed(U0, dims, nc, orc), True)]:
+        d = to_dev(U)
+        p = cu.Params.defaults(nc, dims, precision=cu.DF)
+        cu.culgt_sweep(d, p, 1)
+        ref = U.copy()
+        orc.sweep(ref, dims, nc, 1.7, 1)
+        assert_sweep_close(from_dev(d, U.shape), ref, 3.2e-12, good)
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+@pytest.mark.parametrize("precision", ["df", "mixed_df"])
+def test_landau_fix_double_float(cu, orc, nc, precision):
+    """Double-float polish: theta < 1e-12 measured in FP64 on the stored
+    pairs, F within 1e-10 of the FP64 oracle, plaquette unchanged to 1e-12."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_config(dims, nc, 0.3, 1)
+    d = to_dev(U)
+    prec = cu.DF if precision == "df" else cu.MIXED_DF
+    p = cu.Params.defaults(nc, dims, precision=prec, check_every=5, reunit_every=50, max_sweeps=3000)
+    r = cu.culgt_landau_fix(d, p)
+    ref = U.copy()
+    rr = orc.landau_fix(ref, dims, nc, 1.7, 1e-12, 3000, 1)
+    assert r.status == cu.OK and r.theta < 1e-12
+    assert r.F == pytest.approx(rr["F"], rel=1e-10)
+    assert r.plaq_after == pytest.approx(r.plaq_before, abs=1e-12)
+    th, F = orc.theta(from_dev(d, U.shape), dims, nc)
+    assert th < 1e-12 and F == pytest.approx(r.F, rel=1e-12)
+
+
 @pytest.mark.parametrize("nc", [2, 3])
 def test_float_canonical_buffer(cu, orc, nc):
     dims = (4, 4, 4, 4)
@@ -309,3 +343,42 @@ def test_full_size_32_one_sweep(cu, orc, nc):
         cu.culgt_sweep(d, cu.Params.defaults(nc, dims, precision=cu.FP32), 1)
         assert_sweep_close(from_dev(d, X.shape), ref, 5e-6, good)
         del d
+
+
+@pytest.mark.parametrize("nc,precision,storage", [(3, 0, 18), (3, 0, 12), (3, 1, 12), (3, 1, 18), (3, 4, 0),
+                                                  (2, 0, 4), (2, 1, 4), (2, 4, 0), (3, 2, 12), (2, 2, 4)])
+def test_every_mapping_gives_identical_links(cu, nc, precision, storage):
+    """The autotuner's choices (1 or 2 threads per site, 64/128/256 threads per
+    block) all form K in the same order, so the links agree bit for bit (the
+    mixed cases cover the FP32 phase that also accumulates g)."""
+    dims = (6, 4, 6, 10)
+    U = synth.gauge_config(dims, nc, 0.3, 9)
+    outs = []
+    for tps in (1, 2):
+        for block in (64, 128, 256):
+            p = cu.Params.defaults(nc, dims, precision=precision, storage_reals=storage, threads_per_site=tps,
+                                   block_size=block)
+            d = to_dev(U)
+            with cu.Handle(p) as h:
+                h.culgt_load(d)
+                assert h.culgt_handle_tuning() == (tps, block)
+                h.culgt_handle_sweep(2)
+                if precision == 2:
+                    h.culgt_handle_to_fp64()
+                    h.culgt_handle_sweep(1)
+                out = torch.empty_like(d)
+                h.culgt_store(out)
+                torch.cuda.synchronize()
+            outs.append(out)
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+
+
+def test_autotuner_picks_a_valid_mapping(cu):
+    dims = (16, 16, 16, 32)
+    U = synth.gauge_config(dims, 3, 0.3, 1)
+    for prec in (cu.FP32, cu.FP64, cu.DF):
+        with cu.Handle(cu.Params.defaults(3, dims, precision=prec)) as h:
+            h.culgt_load(to_dev(U))
+            tps, block = h.culgt_handle_tuning()
+            assert tps in (1, 2) and block in (64, 128, 256)
