@@ -43,6 +43,15 @@ WORKLOADS = {
     "su3_4x4x4x4": ((4, 4, 4, 4), 3, 0.3, 1, 1.7),
 }
 
+# batched workloads (not the default line): Gribov copies of 16^4 plus uneven
+# lattices in shared launches, and Coulomb gauge on 48^3 x 96 (one problem per
+# time slice)
+BATCHED = {
+    "gribov_su3_16x16x16x16_64copies_uneven": [((16, 16, 16, 16), 64), ((8, 8, 8, 8), 8), ((12, 12, 12, 12), 8),
+                                               ((32, 16, 16, 16), 8), ((24, 24, 24, 24), 8)],
+    "coulomb_su3_48x48x48x96": None,
+}
+
 # algorithmic bytes per site update: 8 links read + 8 written
 # algorithmic FP64 flops per site update (FMA = 2): SU(3) = gather 126 +
 # subgroup steps 108 + row rotations 336 + eight 3x3 complex products 1584
@@ -61,7 +70,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="culgt", choices=["culgt", "reference"])
-    ap.add_argument("--workload", default="su3_32x32x32x32", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="su3_32x32x32x32", choices=sorted(WORKLOADS) + sorted(BATCHED))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-step", choices=["mixed", "fp64", "fp32", "df", "mixed_df"], default=None,
                     help="run one gauge fixing (or --profile-sweeps sweeps) of the workload and exit; "
@@ -261,6 +270,82 @@ def run_profile_step(args):
         h.culgt_store(d_out)
         torch.cuda.synchronize()
     print(json.dumps({"profile_step": args.profile_step, "workload": args.workload, **out}), flush=True)
+    return 0
+
+
+def run_batched_workload(args):
+    """Gribov-copy search or Coulomb gauge through the batched engine: mixed
+    FP32 -> FP64 against plain FP64, time to theta < 1e-12 for every problem."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1412_3655_gb300 import culgt, synth
+    dev = torch.device("cuda", 0)
+    nc, eps, omega = 3, 0.3, 1.7
+    if args.workload.startswith("gribov"):
+        dims_list, groups, inputs = [], [], []
+        for dims, copies in BATCHED[args.workload]:
+            for c in range(1, copies + 1):
+                U = synth.gauge_config(dims, nc, eps, 4, copy=c)
+                inputs.append(torch.from_numpy(U.view(np.float64).copy()))
+                dims_list.append(dims)
+                groups.append("x".join(map(str, dims)))
+        sites = sum(int(np.prod(d)) for d in dims_list)
+
+        def run(prec):
+            ds = [t.to(dev) for t in inputs]
+            p = culgt.Params.defaults(nc, dims_list[0], omega=omega, precision=prec, check_every=10,
+                                      reunit_every=50, max_sweeps=20000)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = culgt.culgt_fix_batched(ds, dims_list, p)
+            torch.cuda.synchronize()
+            return time.perf_counter() - t0, res, [sum(int(np.prod(d)) for d in [dd]) for dd in dims_list]
+    else:
+        dims = (96, 48, 48, 48)
+        U = synth.gauge_config(dims, nc, eps, 5)
+        host = torch.from_numpy(U.view(np.float64).copy())
+        sites = int(np.prod(dims))
+        groups = [f"t={t}" for t in range(dims[0])]
+
+        def run(prec):
+            d = host.to(dev)
+            p = culgt.Params.defaults(nc, dims, omega=omega, precision=prec, check_every=10, reunit_every=50,
+                                      max_sweeps=20000)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = culgt.culgt_coulomb_fix(d, p)
+            torch.cuda.synchronize()
+            return time.perf_counter() - t0, res, [sites // dims[0]] * dims[0]
+
+    run(culgt.MIXED)  # warm-up (autotuning, graph capture)
+    t_mixed, r_mixed, per = run(culgt.MIXED)
+    t_fp64, r_fp64, _ = run(culgt.FP64)
+    updates = sum((r.sweeps_fp32 + r.sweeps_fp64) * n for r, n in zip(r_mixed, per))
+    maxF = {}
+    for g, r in zip(groups, r_mixed):
+        maxF[g] = max(maxF.get(g, -1.0), r.F)
+    line = {
+        "metric": METRIC, "value": updates / t_mixed, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": 1e3 * t_mixed, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32->f64 (mixed)", "data": "synthetic",
+        "config": {"workload": args.workload, "problems": len(r_mixed), "sites": sites, "eps": eps,
+                   "omega": omega, "theta_target": 1e-12, "switch_theta": 1e-8},
+        "time_to_theta": {"mixed_s": t_mixed, "fp64_s": t_fp64},
+        "all_converged": {"mixed": all(r.status == culgt.OK for r in r_mixed),
+                          "fp64": all(r.status == culgt.OK for r in r_fp64)},
+        "sweeps_mixed": {"fp32_min": min(r.sweeps_fp32 for r in r_mixed),
+                         "fp32_max": max(r.sweeps_fp32 for r in r_mixed),
+                         "fp64_min": min(r.sweeps_fp64 for r in r_mixed),
+                         "fp64_max": max(r.sweeps_fp64 for r in r_mixed)},
+        "max_F": maxF if len(maxF) <= 8 else None,
+        "F_range": [min(r.F for r in r_mixed), max(r.F for r in r_mixed)],
+        "mixed_vs_fp64_max_dF": max(abs(a.F - b.F) for a, b in zip(r_mixed, r_fp64)),
+        "plaquette_drift_max": max(abs(r.plaq_after - r.plaq_before) for r in r_mixed),
+    }
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -465,6 +550,8 @@ def main():
         return run_reference(args)
     if args.profile_step:
         return run_profile_step(args)
+    if args.workload in BATCHED:
+        return run_batched_workload(args)
     return run_culgt(args)
 
 

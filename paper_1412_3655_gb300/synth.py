@@ -169,35 +169,70 @@ def random_gauge(L, nc: int, seed: int, copy: int = 0) -> np.ndarray:
     return haar(sites, nc, seed, SLOT_G if copy == 0 else SLOT_COPY, copy)
 
 
+def _gauge_at(sites, L, nc, seed, copy, spread):
+    """g at the given sites: Haar (spread None) or exp(i spread H), then for
+    copy > 0 the copy's Haar transformation on top, as (g, h) pair."""
+    if spread is None:
+        g = haar(sites, nc, seed, SLOT_G, 0)
+    else:
+        T = generators(nc)
+        c = _gaussians(sites, SLOT_COPY, T.shape[0], seed, 1 << 20)
+        g = expi(np.einsum("na,aij->nij", c, T), spread)
+    h = haar(sites, nc, seed, SLOT_COPY, copy) if copy else None
+    return g, h
+
+
+def _forward_sites(L, sites, mu):
+    L0, L1, L2, L3 = L
+    x1 = sites % L1
+    x2 = (sites // L1) % L2
+    x3 = (sites // (L1 * L2)) % L3
+    x0 = sites // (L1 * L2 * L3)
+    x = [x0, x1, x2, x3]
+    x[mu] = (x[mu] + 1) % L[mu]
+    return x[1] + L1 * (x[2] + L2 * (x[3] + L3 * x[0]))
+
+
+def _links_for_sites(L, nc, eps, seed, copy, g, h, start, stop):
+    """U_mu(x) for the sites x in [start, stop), all mu: (n, 4, Nc, Nc), from
+    the gauge transformations g (and h for copy > 0) of every site."""
+    sites = np.arange(start, stop, dtype=np.int64)
+    n = sites.shape[0]
+    T = generators(nc)
+    out = np.empty((n, 4, nc, nc), dtype=np.complex128)
+    for mu in range(4):
+        if eps == 0.0:
+            E = np.broadcast_to(np.eye(nc, dtype=np.complex128), (n, nc, nc))
+        else:
+            c = _gaussians(sites, SLOT_H + mu, T.shape[0], seed, 0)
+            E = expi(np.einsum("na,aij->nij", c, T), eps)
+        fwd = _forward_sites(L, sites, mu)
+        U = g[start:stop] @ E @ g[fwd].conj().transpose(0, 2, 1)
+        if copy:
+            U = h[start:stop] @ U @ h[fwd].conj().transpose(0, 2, 1)
+        out[:, mu] = U
+    return out
+
+
 def gauge_config(L, nc: int, eps: float, seed: int, copy: int = 0, chunk: int = 1 << 18,
                  spread: float | None = None) -> np.ndarray:
     """U_mu(x) = g(x) exp(i eps H_mu(x)) g(x+mu)^+ with Haar g, as (V, 4, Nc, Nc) complex128.
 
     copy > 0 returns the same configuration under a further Haar-random gauge
     transformation (an independent starting point on the same gauge orbit).
-    spread replaces the Haar g by g = exp(i spread H(x)), a gauge close to 1."""
+    spread replaces the Haar g by g = exp(i spread H(x)), a gauge close to 1.
+    Every site is computed from its own counters, so the result does not
+    depend on chunk (the number of sites done at once)."""
     L = tuple(int(v) for v in L)
     if len(L) != 4 or any(v < 2 for v in L):
         raise ValueError("dims must be four extents >= 2")
     V = int(np.prod(L))
-    T = generators(nc)
-    ncoef = T.shape[0]
-    g = random_gauge(L, nc, seed, 0) if spread is None else near_identity_gauge(L, nc, seed, spread)
     U = np.empty((V, 4, nc, nc), dtype=np.complex128)
+    g, h = _gauge_at(np.arange(V, dtype=np.int64), L, nc, seed, copy, spread)
     for start in range(0, V, chunk):
-        sites = np.arange(start, min(V, start + chunk), dtype=np.int64)
-        for mu in range(4):
-            if eps == 0.0:
-                E = np.broadcast_to(np.eye(nc, dtype=np.complex128), (sites.shape[0], nc, nc))
-            else:
-                c = _gaussians(sites, SLOT_H + mu, ncoef, seed, 0)
-                H = np.einsum("na,aij->nij", c, T)
-                E = expi(H, eps)
-            U[start:start + sites.shape[0], mu] = E
-    U = gauge_transform(U, L, g)
-    if copy:
-        U = gauge_transform(U, L, random_gauge(L, nc, seed, copy))
-    return np.ascontiguousarray(U)
+        stop = min(V, start + chunk)
+        U[start:stop] = _links_for_sites(L, nc, eps, seed, copy, g, h, start, stop)
+    return U
 
 
 def near_identity_gauge(L, nc: int, seed: int, spread: float) -> np.ndarray:
