@@ -302,7 +302,7 @@ def run_batched_workload(args):
             t0 = time.perf_counter()
             res = culgt.culgt_fix_batched(ds, dims_list, p)
             torch.cuda.synchronize()
-            return time.perf_counter() - t0, res, [sum(int(np.prod(d)) for d in [dd]) for dd in dims_list]
+            return time.perf_counter() - t0, res, [int(np.prod(d)) for d in dims_list]
     else:
         dims = (96, 48, 48, 48)
         U = synth.gauge_config(dims, nc, eps, 5)
