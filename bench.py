@@ -79,6 +79,7 @@ def parse():
                     help="with --profile-step: this many sweeps instead of a whole fix")
     ap.add_argument("--tps", type=int, default=0, help="with --profile-step: threads per site (0 = autotune)")
     ap.add_argument("--block", type=int, default=0, help="with --profile-step: threads per block (0 = autotune)")
+    ap.add_argument("--minb", type=int, default=0, help="with --profile-step: min blocks per SM (0 = autotune)")
     return ap.parse_args()
 
 
@@ -257,7 +258,8 @@ def run_profile_step(args):
     prec = {"mixed": culgt.MIXED, "fp64": culgt.FP64, "fp32": culgt.FP32, "df": culgt.DF,
             "mixed_df": culgt.MIXED_DF}[args.profile_step]
     p = culgt.Params.defaults(nc, dims, omega=omega, precision=prec, check_every=10, reunit_every=50,
-                              max_sweeps=20000, threads_per_site=args.tps, block_size=args.block)
+                              max_sweeps=20000, threads_per_site=args.tps, block_size=args.block,
+                              min_blocks_per_sm=args.minb)
     with culgt.Handle(p) as h:
         h.culgt_load(d_in)
         if args.profile_sweeps:
@@ -438,21 +440,21 @@ def run_culgt(args):
     share32 = last.sweeps_fp32 * t32
     share64 = last.sweeps_fp64 * t64
 
-    def roofline_hbm(key, t_ms, tps):
+    def roofline_hbm(key, t_ms, m):
         bytes_launch = (V // 2) * BYTES_PER_SITE[key]
         achieved = bytes_launch / (t_ms / 1e3) / 1e9
         name = (f"halfsweep_su{nc}_{'f32' if key[1] else 'f64'}_{key[2]}" + ("_acc" if len(key) > 3 else "")
-                + f"_tps{tps}")
+                + f"_tps{m[0]}_mb{m[2]}")
         return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": recorded_traffic(name), "kernel": name, "launch_ms": t_ms,
                 "algorithmic_bytes_per_launch": bytes_launch, "peak_source": f"{peak_src} hbm_gbs"}
 
-    def roofline_fp64(key, t_ms, tps):
+    def roofline_fp64(key, t_ms, m):
         # FP64-ALU bound on GB300: algorithmic FP64 flops per SU(3) site update
         # (FMA = 2) against 2 DFMA/clock/SM x 152 SMs x 2070 MHz
         flops_launch = (V // 2) * FLOPS_PER_SITE[nc]
         achieved = flops_launch / (t_ms / 1e3) / 1e12
-        name = f"halfsweep_su{nc}_{'f32' if key[1] else 'f64'}_{key[2]}_tps{tps}"
+        name = f"halfsweep_su{nc}_{'f32' if key[1] else 'f64'}_{key[2]}_tps{m[0]}_mb{m[2]}"
         return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(name), "kernel": name,
                 "launch_ms": t_ms, "algorithmic_flops_per_launch": flops_launch,
@@ -460,8 +462,8 @@ def run_culgt(args):
                 "hbm_frac": (V // 2) * BYTES_PER_SITE[key] / (t_ms / 1e3) / 1e9 / hbm,
                 "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (unit counts and max clock)"}
 
-    rl32 = roofline_hbm((nc, 1, 12 if nc == 3 else 4, "acc"), t32, mapping["fp32_phase"][0])
-    rl64 = roofline_fp64((nc, 0, 18 if nc == 3 else 4), t64, mapping["fp64"][0])
+    rl32 = roofline_hbm((nc, 1, 12 if nc == 3 else 4, "acc"), t32, mapping["fp32_phase"])
+    rl64 = roofline_fp64((nc, 0, 18 if nc == 3 else 4), t64, mapping["fp64"])
     dominant = rl32 if share32 >= share64 else rl64
     dominant = dict(dominant, time_share_in_step=max(share32, share64) / max(share32 + share64, 1e-30))
 
@@ -485,7 +487,7 @@ def run_culgt(args):
     mixed_df_s, rmd = fix_time(mixed_df)
     df_s, rdf = fix_time(only_df)
     tdf = kernel_ms(only_df, 20)
-    rldf = roofline_hbm((nc, 0, 18 if nc == 3 else 4), tdf, mapping["double_float"][0])
+    rldf = roofline_hbm((nc, 0, 18 if nc == 3 else 4), tdf, mapping["double_float"])
     rldf["kernel"] = rldf["kernel"].replace("f64", "df")
     rldf["traffic"] = recorded_traffic(rldf["kernel"])
     # the FP32 -> FP64 switch later: the orbit-exact switch keeps the FP32
@@ -529,7 +531,8 @@ def run_culgt(args):
         "roofline": dominant,
         "roofline_kernels": {"fp32_phase": rl32, "fp64": rl64, "double_float": rldf},
         "gpu_launches": launches,
-        "sweep_mapping": {k: {"threads_per_site": v[0], "block": v[1]} for k, v in mapping.items()},
+        "sweep_mapping": {k: {"threads_per_site": v[0], "block": v[1], "min_blocks_per_sm": v[2]}
+                          for k, v in mapping.items()},
         "e2e": {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": canon_bytes,
                 "d2h_bytes_per_step": canon_bytes, "steps": n_e2e},
         "clocks": clocks,

@@ -83,6 +83,8 @@ typedef struct {
     int dtype_in;        /* canonical link buffer element type: 0 = double, 1 = float */
     int threads_per_site; /* half-sweep mapping: 1 or 2 threads per site; 0 = autotune */
     int block_size;       /* half-sweep threads per block: 64, 128 or 256; 0 = autotune */
+    int min_blocks_per_sm; /* register limit: 1 = none, 3 or 4 blocks of 128 per SM (at most 168 / 128
+                              registers, block_size 128); 0 = autotune */
 } culgt_params;
 
 typedef struct {
@@ -144,10 +146,13 @@ culgt_status culgt_handle_reunitarize(culgt_handle *h);
  * culgt_load, so FP32 rounding never moves the links off the gauge orbit of
  * the input (the plaquette is kept to FP64 rounding). No-op in FP64. */
 culgt_status culgt_handle_to_fp64(culgt_handle *h);
-/* The half-sweep mapping the handle uses (after autotuning, which happens at
- * the first sweep unless threads_per_site and block_size are both set). The
- * mappings give bitwise identical links; only their speed differs. */
-culgt_status culgt_handle_tuning(culgt_handle *h, int *threads_per_site, int *block_size);
+/* The half-sweep mapping the handle uses. Unless the parameters fix a single
+ * mapping, the first sweep times every allowed one (threads per site, block
+ * size, register limit; Sec. 5's autotuner) on a scratch copy of the links
+ * and keeps the fastest for this storage and volume in the process. Lattices
+ * below 65536 sites take the first allowed mapping untimed. The mappings give
+ * bitwise identical links; only their speed differs. */
+culgt_status culgt_handle_tuning(culgt_handle *h, int *threads_per_site, int *block_size, int *min_blocks_per_sm);
 /* Iterates to theta_target as the precision field says (mixed: FP32 until
  * theta < switch_theta, then FP64). Leaves the result in the handle. */
 culgt_status culgt_handle_fix(culgt_handle *h, culgt_result *out);

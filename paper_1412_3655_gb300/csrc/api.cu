@@ -31,7 +31,8 @@ struct culgt_handle {
     void *staging;      // canonical device buffer for the host entry point
     void *gacc;         // mixed: FP32 accumulated gauge transformation per site
     int sweeps32, sweeps64;
-    int tps32, block32, tps64, block64;  // half-sweep mapping per precision (0 = not chosen yet)
+    // half-sweep mapping per precision: threads per site, block, blocks per SM (0 = not chosen yet)
+    int tps32, block32, minb32, tps64, block64, minb64;
 };
 
 namespace {
@@ -75,6 +76,9 @@ culgt_status validate(const culgt_params *p)
     if (p->dtype_in != 0 && p->dtype_in != 1) return CULGT_ERR_ARG;
     if (p->threads_per_site < 0 || p->threads_per_site > 2) return CULGT_ERR_ARG;
     if (p->block_size != 0 && p->block_size != 64 && p->block_size != 128 && p->block_size != 256) return CULGT_ERR_ARG;
+    if (p->min_blocks_per_sm != 0 && p->min_blocks_per_sm != 1 && p->min_blocks_per_sm != 3 &&
+        p->min_blocks_per_sm != 4)
+        return CULGT_ERR_ARG;
     return CULGT_OK;
 }
 
@@ -163,24 +167,47 @@ culgt_status unitarity_now(culgt_handle *h, double *err)
 // changes a result. Lattices below kTuneMinSites use the default mapping.
 constexpr int kTuneMinSites = 1 << 16;
 std::mutex g_tune_mutex;
-std::map<std::tuple<const Ops *, int, bool>, std::pair<int, int>> g_tune_cache;
 
-culgt_status autotune(culgt_handle *h, const Ops *o, void *buf, bool acc, int *tps_out, int *block_out)
+struct Mapping {
+    int tps, block, minb;
+};
+std::map<std::tuple<const Ops *, int, bool, int>, Mapping> g_tune_cache;
+
+// the mappings the autotuner tries (the paper's axes: threads per site and a
+// register limit through __launch_bounds__; plus the block size)
+const Mapping kMappings[] = {{1, 64, 1}, {1, 128, 1}, {1, 256, 1}, {1, 128, 3}, {1, 128, 4},
+                             {2, 64, 1},  {2, 128, 1}, {2, 256, 1}, {2, 128, 4}};
+
+bool mapping_allowed(const culgt_params &p, const Mapping &m)
+{
+    if (p.threads_per_site && m.tps != p.threads_per_site) return false;
+    if (p.block_size && m.block != p.block_size) return false;
+    if (p.min_blocks_per_sm && m.minb != p.min_blocks_per_sm) return false;
+    return true;
+}
+
+culgt_status autotune(culgt_handle *h, const Ops *o, void *buf, bool acc, Mapping *out)
 {
     const culgt_params &p = h->prm;
-    int tps = p.threads_per_site ? p.threads_per_site : 1, block = p.block_size ? p.block_size : 128;
-    if ((p.threads_per_site && p.block_size) || h->geom.V < kTuneMinSites) {
-        *tps_out = tps;
-        *block_out = block;
+    int n_allowed = 0;
+    Mapping only = {1, 128, 1};
+    for (const Mapping &m : kMappings)
+        if (mapping_allowed(p, m)) {
+            if (!n_allowed) only = m;
+            n_allowed++;
+        }
+    if (!n_allowed) return CULGT_ERR_ARG;
+    if (n_allowed == 1 || h->geom.V < kTuneMinSites) {
+        // small lattices: the first allowed mapping in the list
+        *out = only;
         return CULGT_OK;
     }
-    auto key = std::make_tuple(o, h->geom.V, acc);
+    auto key = std::make_tuple(o, h->geom.V, acc, p.threads_per_site * 10000 + p.block_size * 10 + p.min_blocks_per_sm);
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            *tps_out = p.threads_per_site ? p.threads_per_site : it->second.first;
-            *block_out = p.block_size ? p.block_size : it->second.second;
+            *out = it->second;
             return CULGT_OK;
         }
     }
@@ -198,26 +225,23 @@ culgt_status autotune(culgt_handle *h, const Ops *o, void *buf, bool acc, int *t
     CU(cudaMemcpyAsync(scratch, buf, bytes, cudaMemcpyDeviceToDevice, h->stream));
     if (acc) CU(cudaMemcpyAsync(gscratch, h->gacc, gbytes, cudaMemcpyDeviceToDevice, h->stream));
     float best = 1e30f;
-    int best_tps = tps, best_block = block;
-    for (int t = 1; t <= 2; t++) {
-        if (p.threads_per_site && t != p.threads_per_site) continue;
-        for (int b : {64, 128, 256}) {
-            if (p.block_size && b != p.block_size) continue;
-            o->halfsweep(scratch, gscratch, h->geom, 0, p.omega, p.or_variant, t, b, h->stream);
-            cudaEventRecord(e0, h->stream);
-            for (int r = 0; r < 2; r++)
-                for (int parity = 0; parity < 2; parity++)
-                    o->halfsweep(scratch, gscratch, h->geom, parity, p.omega, p.or_variant, t, b, h->stream);
-            cudaEventRecord(e1, h->stream);
-            cudaEventSynchronize(e1);
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            count_launch(-5);  // tuning launches are not part of the caller's work
-            if (ms < best) {
-                best = ms;
-                best_tps = t;
-                best_block = b;
-            }
+    Mapping pick = only;
+    for (const Mapping &m : kMappings) {
+        if (!mapping_allowed(p, m)) continue;
+        o->halfsweep(scratch, gscratch, h->geom, 0, p.omega, p.or_variant, m.tps, m.block, m.minb, h->stream);
+        cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < 2; r++)
+            for (int parity = 0; parity < 2; parity++)
+                o->halfsweep(scratch, gscratch, h->geom, parity, p.omega, p.or_variant, m.tps, m.block, m.minb,
+                             h->stream);
+        cudaEventRecord(e1, h->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        count_launch(-5);  // tuning launches are not part of the caller's work
+        if (ms < best) {
+            best = ms;
+            pick = m;
         }
     }
     cudaEventDestroy(e0);
@@ -226,35 +250,40 @@ culgt_status autotune(culgt_handle *h, const Ops *o, void *buf, bool acc, int *t
     CU(cudaGetLastError());
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
-        g_tune_cache[key] = std::make_pair(best_tps, best_block);
+        g_tune_cache[key] = pick;
     }
-    *tps_out = best_tps;
-    *block_out = best_block;
+    *out = pick;
     return CULGT_OK;
 }
 
-culgt_status tuned_mapping(culgt_handle *h, int *tps, int *block)
+culgt_status tuned_mapping(culgt_handle *h, Mapping *m)
 {
     const bool acc = h->cur32 && h->gacc;
-    int &t = h->cur32 ? h->tps32 : h->tps64;
-    int &b = h->cur32 ? h->block32 : h->block64;
-    if (!t) ST(autotune(h, cur_ops(h), cur_buf(h), acc, &t, &b));
-    *tps = t;
-    *block = b;
+    int *t = h->cur32 ? &h->tps32 : &h->tps64;
+    int *b = h->cur32 ? &h->block32 : &h->block64;
+    int *n = h->cur32 ? &h->minb32 : &h->minb64;
+    if (!*t) {
+        Mapping pick;
+        ST(autotune(h, cur_ops(h), cur_buf(h), acc, &pick));
+        *t = pick.tps;
+        *b = pick.block;
+        *n = pick.minb;
+    }
+    *m = {*t, *b, *n};
     return CULGT_OK;
 }
 
 // In the FP32 phase of a mixed handle the half-sweeps also accumulate g(x).
 culgt_status sweep_now(culgt_handle *h, int n)
 {
-    int tps, block;
-    ST(tuned_mapping(h, &tps, &block));
+    Mapping m;
+    ST(tuned_mapping(h, &m));
     const Ops *o = cur_ops(h);
     void *b = cur_buf(h);
     void *acc = (h->cur32 && h->gacc) ? h->gacc : nullptr;
     for (int k = 0; k < n; k++)
         for (int parity = 0; parity < 2; parity++)
-            o->halfsweep(b, acc, h->geom, parity, h->prm.omega, h->prm.or_variant, tps, block, h->stream);
+            o->halfsweep(b, acc, h->geom, parity, h->prm.omega, h->prm.or_variant, m.tps, m.block, m.minb, h->stream);
     return CULGT_OK;
 }
 
@@ -519,10 +548,15 @@ culgt_status culgt_handle_to_fp64(culgt_handle *h)
     return CULGT_OK;
 }
 
-culgt_status culgt_handle_tuning(culgt_handle *h, int *threads_per_site, int *block_size)
+culgt_status culgt_handle_tuning(culgt_handle *h, int *threads_per_site, int *block_size, int *min_blocks_per_sm)
 {
-    if (!h || !h->loaded || !threads_per_site || !block_size) return CULGT_ERR_ARG;
-    return tuned_mapping(h, threads_per_site, block_size);
+    if (!h || !h->loaded || !threads_per_site || !block_size || !min_blocks_per_sm) return CULGT_ERR_ARG;
+    Mapping m;
+    ST(tuned_mapping(h, &m));
+    *threads_per_site = m.tps;
+    *block_size = m.block;
+    *min_blocks_per_sm = m.minb;
+    return CULGT_OK;
 }
 
 culgt_status culgt_handle_fix(culgt_handle *h, culgt_result *out)

@@ -199,10 +199,13 @@ template <class P> struct KeepLinks2 {
 };
 
 // Half-sweep with TPS threads per site (thread t: site t / TPS, half t % TPS);
-// ACC: also accumulate gacc(x) <- g(x) gacc(x) (mixed FP32 phase)
-template <class P, int TPS, class PG>
-__global__ void __launch_bounds__(256) k_halfsweep_v(typename P::Chunk *base, typename PG::Chunk *gacc, Geom g,
-                                                     int parity, typename P::Real omega, int variant, int acc)
+// acc: also accumulate gacc(x) <- g(x) gacc(x) (mixed FP32 phase). MAXT and
+// MINB are the launch bounds: MINB > 1 caps the registers at
+// 65536 / (MAXT MINB) so that MINB blocks fit on an SM (the autotuner's
+// register-limit axis).
+template <class P, int TPS, class PG, int MAXT = 256, int MINB = 1>
+__global__ void __launch_bounds__(MAXT, MINB) k_halfsweep_v(typename P::Chunk *base, typename PG::Chunk *gacc, Geom g,
+                                                           int parity, typename P::Real omega, int variant, int acc)
 {
     typedef typename P::Real T;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;

@@ -28,10 +28,11 @@ struct Ops {
     int nchunk;     // chunks per link
     int chunk_bytes;
     // one checkerboard half-sweep of the given parity, tps (1 or 2) threads per
-    // site in blocks of `block` threads; gacc != null (FP32 storage) also
-    // accumulates g(x) per site. Every (tps, block) gives the same result.
+    // site in blocks of `block` threads, minb blocks of 128 per SM (1: no
+    // register cap; 3 or 4: block must be 128); gacc != null (FP32 storage)
+    // also accumulates g(x) per site. Every mapping gives the same result.
     void (*halfsweep)(void *base, void *gacc, const Geom &g, int parity, double omega, int variant, int tps,
-                      int block, cudaStream_t s);
+                      int block, int minb, cudaStream_t s);
     // per-block partial sums of (tr Delta Delta^+, sum Re tr U) over all sites; returns the block count
     int (*theta_partials)(const void *base, const Geom &g, int mu_first, double2 *partials, cudaStream_t s);
     // per-block partial sums of the plaquette trace; returns the block count

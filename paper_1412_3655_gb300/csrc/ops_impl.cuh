@@ -18,21 +18,29 @@ template <class P> struct OpsImpl {
     static constexpr int kThetaThreads = 256;
     static constexpr int kPlaqThreads = 128;
 
-    // tps threads per site, block threads per block; gacc != null also
-    // accumulates g (FP32 storage)
+    // tps threads per site, block threads per block, minb: 1 (no register
+    // cap) or 3 / 4 blocks of 128 threads per SM (registers capped at 168 /
+    // 128); gacc != null also accumulates g (FP32 storage)
     static void halfsweep(void *base, void *gacc, const Geom &g, int parity, double omega, int variant, int tps,
-                          int block, cudaStream_t s)
+                          int block, int minb, cudaStream_t s)
     {
         typedef typename GaugeParam<P>::type PG;
         typedef typename PG::Chunk GC;
         const typename P::Real w = (typename P::Real)omega;
         const int acc = gacc != nullptr;
-        if (tps == 2)
-            k_halfsweep_v<P, 2, PG><<<blocks_for(2LL * g.Vh, block), block, 0, s>>>((C *)base, (GC *)gacc, g, parity,
-                                                                                   w, variant, acc);
+        const unsigned nb = blocks_for((long long)tps * g.Vh, block);
+        C *b = (C *)base;
+        GC *a = (GC *)gacc;
+        if (tps == 2 && minb == 4)
+            k_halfsweep_v<P, 2, PG, 128, 4><<<nb, 128, 0, s>>>(b, a, g, parity, w, variant, acc);
+        else if (tps == 2)
+            k_halfsweep_v<P, 2, PG><<<nb, block, 0, s>>>(b, a, g, parity, w, variant, acc);
+        else if (minb == 4)
+            k_halfsweep_v<P, 1, PG, 128, 4><<<nb, 128, 0, s>>>(b, a, g, parity, w, variant, acc);
+        else if (minb == 3)
+            k_halfsweep_v<P, 1, PG, 128, 3><<<nb, 128, 0, s>>>(b, a, g, parity, w, variant, acc);
         else
-            k_halfsweep_v<P, 1, PG><<<blocks_for(g.Vh, block), block, 0, s>>>((C *)base, (GC *)gacc, g, parity, w,
-                                                                              variant, acc);
+            k_halfsweep_v<P, 1, PG><<<nb, block, 0, s>>>(b, a, g, parity, w, variant, acc);
         count_launch();
     }
     static int theta_partials(const void *base, const Geom &g, int mu_first, double2 *partials, cudaStream_t s)

@@ -45,6 +45,7 @@ class _Params(ctypes.Structure):
         ("dtype_in", ctypes.c_int),
         ("threads_per_site", ctypes.c_int),
         ("block_size", ctypes.c_int),
+        ("min_blocks_per_sm", ctypes.c_int),
     ]
 
 
@@ -82,6 +83,7 @@ class Params:
     dtype_in: int = 0
     threads_per_site: int = 0
     block_size: int = 0
+    min_blocks_per_sm: int = 0
 
     @classmethod
     def defaults(cls, nc, dims, **kw):
@@ -143,7 +145,8 @@ def library():
         "culgt_handle_reunitarize": (ip, [H]),
         "culgt_handle_to_fp64": (ip, [H]),
         "culgt_handle_fix": (ip, [H, R]),
-        "culgt_handle_tuning": (ip, [H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+        "culgt_handle_tuning": (ip, [H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int)]),
         "culgt_landau_fix": (ip, [vp, P, vp, R]),
         "culgt_landau_fix_host": (ip, [vp, P, vp, R]),
         "culgt_sweep": (ip, [vp, P, ip, vp]),
@@ -364,9 +367,11 @@ class Handle:
         _check(library().culgt_handle_to_fp64(self._h), "culgt_handle_to_fp64")
 
     def culgt_handle_tuning(self):
-        t, b = ctypes.c_int(), ctypes.c_int()
-        _check(library().culgt_handle_tuning(self._h, ctypes.byref(t), ctypes.byref(b)), "culgt_handle_tuning")
-        return t.value, b.value
+        """(threads per site, block size, min blocks per SM) of the half-sweeps."""
+        t, b, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(library().culgt_handle_tuning(self._h, ctypes.byref(t), ctypes.byref(b), ctypes.byref(m)),
+               "culgt_handle_tuning")
+        return t.value, b.value, m.value
 
     def culgt_handle_fix(self) -> Result:
         r = _Result()

@@ -65,6 +65,9 @@ def test_defaults_validate(lib):
     ({"theta_target": float("inf")}, -1),
     ({"dtype_in": 2}, -1),
     ({"or_variant": 2}, -1),
+    ({"threads_per_site": 3}, -1),
+    ({"block_size": 96}, -1),
+    ({"min_blocks_per_sm": 2}, -1),
 ])
 def test_validate_rejects(lib, change, code):
     p = lib.Params.defaults(3, (4, 4, 4, 4))

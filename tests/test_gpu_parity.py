@@ -349,19 +349,21 @@ def test_full_size_32_one_sweep(cu, orc, nc):
                                                   (2, 0, 4), (2, 1, 4), (2, 4, 0), (3, 2, 12), (2, 2, 4)])
 def test_every_mapping_gives_identical_links(cu, nc, precision, storage):
     """The autotuner's choices (1 or 2 threads per site, 64/128/256 threads per
-    block) all form K in the same order, so the links agree bit for bit (the
-    mixed cases cover the FP32 phase that also accumulates g)."""
+    block, register limits) all form K in the same order, so the links agree
+    bit for bit (the mixed cases cover the FP32 phase that also accumulates g)."""
     dims = (6, 4, 6, 10)
     U = synth.gauge_config(dims, nc, 0.3, 9)
     outs = []
-    for tps in (1, 2):
-        for block in (64, 128, 256):
+    mappings = [(1, 64, 1), (1, 128, 1), (1, 256, 1), (1, 128, 3), (1, 128, 4), (2, 64, 1), (2, 128, 1),
+                (2, 256, 1), (2, 128, 4)]
+    for tps, block, minb in mappings:
+        if True:
             p = cu.Params.defaults(nc, dims, precision=precision, storage_reals=storage, threads_per_site=tps,
-                                   block_size=block)
+                                   block_size=block, min_blocks_per_sm=minb)
             d = to_dev(U)
             with cu.Handle(p) as h:
                 h.culgt_load(d)
-                assert h.culgt_handle_tuning() == (tps, block)
+                assert h.culgt_handle_tuning() == (tps, block, minb)
                 h.culgt_handle_sweep(2)
                 if precision == 2:
                     h.culgt_handle_to_fp64()
@@ -380,5 +382,5 @@ def test_autotuner_picks_a_valid_mapping(cu):
     for prec in (cu.FP32, cu.FP64, cu.DF):
         with cu.Handle(cu.Params.defaults(3, dims, precision=prec)) as h:
             h.culgt_load(to_dev(U))
-            tps, block = h.culgt_handle_tuning()
-            assert tps in (1, 2) and block in (64, 128, 256)
+            tps, block, minb = h.culgt_handle_tuning()
+            assert tps in (1, 2) and block in (64, 128, 256) and minb in (1, 3, 4)
