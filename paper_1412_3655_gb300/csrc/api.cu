@@ -15,9 +15,22 @@
 
 using namespace culgt;
 
+// CUDA graphs of a handle's check intervals, keyed by (phase, k,
+// reunitarisation offsets): graph exec and the number of kernels in it
+struct GraphCache {
+    std::map<long long, std::pair<cudaGraphExec_t, int>> exec;
+    ~GraphCache()
+    {
+        for (auto &kv : exec) cudaGraphExecDestroy(kv.second.first);
+    }
+};
+
 struct culgt_handle {
     culgt_params prm;
-    cudaStream_t stream;
+    cudaStream_t stream;   // the handle's own stream: all of its work, and graph capture
+    cudaStream_t ustream;  // the caller's stream, ordered against `stream` by events at every call
+    cudaEvent_t ev_in, ev_out;
+    GraphCache *graphs;
     Geom geom;
     const Ops *ops32;  // FP32 storage (FP32 and mixed), else null
     const Ops *ops64;  // FP64 storage (FP64 and mixed), else null
@@ -53,6 +66,22 @@ namespace {
     } while (0)
 
 int default_storage(int nc, int fp32) { return nc == 2 ? 4 : (fp32 ? 12 : 18); }
+
+// Work of a handle call runs on the handle's own stream, after everything
+// already queued on the caller's stream, and the caller's stream waits for it.
+struct CallScope {
+    culgt_handle *h;
+    explicit CallScope(culgt_handle *hh) : h(hh)
+    {
+        cudaEventRecord(h->ev_in, h->ustream);
+        cudaStreamWaitEvent(h->stream, h->ev_in, 0);
+    }
+    ~CallScope()
+    {
+        cudaEventRecord(h->ev_out, h->stream);
+        cudaStreamWaitEvent(h->ustream, h->ev_out, 0);
+    }
+};
 
 culgt_status validate(const culgt_params *p)
 {
@@ -124,13 +153,21 @@ culgt_status sync_scalars(culgt_handle *h, int n)
     return CULGT_OK;
 }
 
-// theta and F of the current links, normalised as in the header (Landau)
-culgt_status theta_now(culgt_handle *h, double *theta, double *F)
+// queue theta and F of the current links into h_scalars (pinned host)
+void theta_enqueue(culgt_handle *h)
 {
     const Geom &g = h->geom;
     int nb = cur_ops(h)->theta_partials(cur_buf(h), g, 0, h->partials, h->stream);
     launch_finalize2(h->partials, nb, 1.0 / g.V, 1.0 / (4.0 * h->prm.nc * g.V), h->d_scalars, h->stream);
-    ST(sync_scalars(h, 2));
+    cudaMemcpyAsync(h->h_scalars, h->d_scalars, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+}
+
+// theta and F of the current links, normalised as in the header (Landau)
+culgt_status theta_now(culgt_handle *h, double *theta, double *F)
+{
+    theta_enqueue(h);
+    CU(cudaStreamSynchronize(h->stream));
+    CU(cudaGetLastError());
     *theta = h->h_scalars[0];
     *F = h->h_scalars[1];
     if (!std::isfinite(*theta) || !std::isfinite(*F)) return CULGT_ERR_NONFINITE;
@@ -293,8 +330,68 @@ void reunitarize_now(culgt_handle *h)
     if (h->cur32 && h->gacc) h->ops32->gauge_reunitarize(h->gacc, h->geom, h->stream);
 }
 
+// One check interval: k sweeps (reunitarising after sweep n + j when due)
+// and the theta of the result, queued into h_scalars.
+culgt_status interval_enqueue(culgt_handle *h, int k, int n)
+{
+    for (int j = 0; j < k; j++) {
+        ST(sweep_now(h, 1));
+        if (h->prm.reunit_every > 0 && (n + j + 1) % h->prm.reunit_every == 0) reunitarize_now(h);
+    }
+    theta_enqueue(h);
+    return CULGT_OK;
+}
+
+// replay the interval's graph, capturing it on first use (after the
+// autotuner has fixed the mapping, which the capture must not time)
+culgt_status run_interval(culgt_handle *h, int k, int n)
+{
+    Mapping m;
+    ST(tuned_mapping(h, &m));
+    long long mask = 0;
+    if (h->prm.reunit_every > 0)
+        for (int j = 0; j < k && j < 40; j++)
+            if ((n + j + 1) % h->prm.reunit_every == 0) mask |= 1LL << j;
+    if (k > 40) {
+        ST(interval_enqueue(h, k, n));
+        CU(cudaGetLastError());
+        return CULGT_OK;
+    }
+    long long key = ((mask * 64 + k) << 1) | (h->cur32 ? 1 : 0);
+    auto it = h->graphs->exec.find(key);
+    if (it == h->graphs->exec.end()) {
+        long long before = launches_so_far();
+        CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        culgt_status st = interval_enqueue(h, k, n);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+        if (st != CULGT_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return CULGT_ERR_CUDA;
+        }
+        cudaGraphExec_t exec;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return CULGT_ERR_CUDA;
+        }
+        int kernels = (int)(launches_so_far() - before);
+        count_launch(-kernels);  // captured, not launched
+        it = h->graphs->exec.emplace(key, std::make_pair(exec, kernels)).first;
+    }
+    CU(cudaGraphLaunch(it->second.first, h->stream));
+    count_launch(it->second.second);
+    return CULGT_OK;
+}
+
 // Sweeps the current links until theta < target or the running total n
 // reaches max_sweeps; theta is measured first and every check_every sweeps.
+// Each check interval is one CUDA graph replay and one host read of theta.
 culgt_status run_phase(culgt_handle *h, double target, int *n, int *phase_sweeps, double *theta, double *F)
 {
     const culgt_params &p = h->prm;
@@ -302,13 +399,14 @@ culgt_status run_phase(culgt_handle *h, double target, int *n, int *phase_sweeps
     while (!(*theta < target) && *n < p.max_sweeps) {
         int k = p.check_every;
         if (k > p.max_sweeps - *n) k = p.max_sweeps - *n;
-        for (int j = 0; j < k; j++) {
-            ST(sweep_now(h, 1));
-            ++*n;
-            ++*phase_sweeps;
-            if (p.reunit_every > 0 && *n % p.reunit_every == 0) reunitarize_now(h);
-        }
-        ST(theta_now(h, theta, F));
+        ST(run_interval(h, k, *n));
+        CU(cudaStreamSynchronize(h->stream));
+        CU(cudaGetLastError());
+        *n += k;
+        *phase_sweeps += k;
+        *theta = h->h_scalars[0];
+        *F = h->h_scalars[1];
+        if (!std::isfinite(*theta) || !std::isfinite(*F)) return CULGT_ERR_NONFINITE;
     }
     return CULGT_OK;
 }
@@ -431,12 +529,18 @@ culgt_status culgt_create(const culgt_params *p, void *cuda_stream, culgt_handle
     if (!h) return CULGT_ERR_OOM;
     std::memset(h, 0, sizeof *h);
     h->prm = *p;
-    h->stream = (cudaStream_t)cuda_stream;
+    h->ustream = (cudaStream_t)cuda_stream;
+    h->graphs = new (std::nothrow) GraphCache;
     h->geom = make_geom(p->dims);
     pick_ops(p, &h->ops32, &h->ops64);
     h->cur32 = h->ops32 != nullptr;
-    culgt_status st = CULGT_OK;
-    if (h->ops32 && cudaMalloc(&h->buf32, buffer_bytes(h->ops32, h->geom)) != cudaSuccess) st = CULGT_ERR_OOM;
+    culgt_status st = h->graphs ? CULGT_OK : CULGT_ERR_OOM;
+    if (st == CULGT_OK && (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
+                           cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+                           cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess))
+        st = CULGT_ERR_CUDA;
+    if (st == CULGT_OK && h->ops32 && cudaMalloc(&h->buf32, buffer_bytes(h->ops32, h->geom)) != cudaSuccess)
+        st = CULGT_ERR_OOM;
     if (st == CULGT_OK && h->ops64 && cudaMalloc(&h->buf64, buffer_bytes(h->ops64, h->geom)) != cudaSuccess)
         st = CULGT_ERR_OOM;
     if (st == CULGT_OK && h->ops32 && h->ops64 && cudaMalloc(&h->gacc, gauge_bytes(h->ops32, h->geom)) != cudaSuccess)
@@ -459,6 +563,11 @@ culgt_status culgt_create(const culgt_params *p, void *cuda_stream, culgt_handle
 void culgt_destroy(culgt_handle *h)
 {
     if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    delete h->graphs;
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->stream) cudaStreamDestroy(h->stream);
     if (h->buf32) cudaFree(h->buf32);
     if (h->buf64) cudaFree(h->buf64);
     if (h->partials) cudaFree(h->partials);
@@ -474,6 +583,7 @@ void culgt_destroy(culgt_handle *h)
 culgt_status culgt_load(culgt_handle *h, const void *d_links)
 {
     if (!h || !d_links) return CULGT_ERR_ARG;
+    CallScope scope(h);
     const Ops *os[2] = {h->ops32, h->ops64};
     void *bs[2] = {h->buf32, h->buf64};
     for (int k = 0; k < 2; k++) {
@@ -493,6 +603,7 @@ culgt_status culgt_load(culgt_handle *h, const void *d_links)
 culgt_status culgt_store(culgt_handle *h, void *d_links)
 {
     if (!h || !d_links || !h->loaded) return CULGT_ERR_ARG;
+    CallScope scope(h);
     const Ops *o = cur_ops(h);
     if (h->prm.dtype_in)
         o->to_canonical_f(cur_buf(h), (float *)d_links, h->geom, h->stream);
@@ -505,6 +616,7 @@ culgt_status culgt_store(culgt_handle *h, void *d_links)
 culgt_status culgt_handle_sweep(culgt_handle *h, int n_sweeps)
 {
     if (!h || !h->loaded || n_sweeps < 0) return CULGT_ERR_ARG;
+    CallScope scope(h);
     ST(sweep_now(h, n_sweeps));
     CU(cudaGetLastError());
     return CULGT_OK;
@@ -513,6 +625,7 @@ culgt_status culgt_handle_sweep(culgt_handle *h, int n_sweeps)
 culgt_status culgt_handle_theta(culgt_handle *h, double *theta, double *F)
 {
     if (!h || !h->loaded) return CULGT_ERR_ARG;
+    CallScope scope(h);
     double t, f;
     culgt_status st = theta_now(h, &t, &f);
     if (theta) *theta = t;
@@ -523,12 +636,14 @@ culgt_status culgt_handle_theta(culgt_handle *h, double *theta, double *F)
 culgt_status culgt_handle_plaquette(culgt_handle *h, double *plaq)
 {
     if (!h || !h->loaded || !plaq) return CULGT_ERR_ARG;
+    CallScope scope(h);
     return plaquette_now(h, plaq);
 }
 
 culgt_status culgt_handle_reunitarize(culgt_handle *h)
 {
     if (!h || !h->loaded) return CULGT_ERR_ARG;
+    CallScope scope(h);
     reunitarize_now(h);
     CU(cudaGetLastError());
     return CULGT_OK;
@@ -537,6 +652,7 @@ culgt_status culgt_handle_reunitarize(culgt_handle *h)
 culgt_status culgt_handle_to_fp64(culgt_handle *h)
 {
     if (!h || !h->loaded) return CULGT_ERR_ARG;
+    CallScope scope(h);
     if (!h->cur32) return CULGT_OK;
     if (!h->ops64) return CULGT_ERR_ARG;  // an FP32-only handle has no FP64 buffer
     if (h->gacc)
@@ -551,6 +667,7 @@ culgt_status culgt_handle_to_fp64(culgt_handle *h)
 culgt_status culgt_handle_tuning(culgt_handle *h, int *threads_per_site, int *block_size, int *min_blocks_per_sm)
 {
     if (!h || !h->loaded || !threads_per_site || !block_size || !min_blocks_per_sm) return CULGT_ERR_ARG;
+    CallScope scope(h);
     Mapping m;
     ST(tuned_mapping(h, &m));
     *threads_per_site = m.tps;
@@ -562,6 +679,7 @@ culgt_status culgt_handle_tuning(culgt_handle *h, int *threads_per_site, int *bl
 culgt_status culgt_handle_fix(culgt_handle *h, culgt_result *out)
 {
     if (!h) return CULGT_ERR_ARG;
+    CallScope scope(h);
     return fix_handle(h, out);
 }
 

@@ -50,9 +50,11 @@ struct BRule {
 };
 
 // site (cb, p) of a problem: the site update of Sec. 2 on its own links, and
-// for PG != void the accumulation gacc(x) <- g(x) gacc(x) in PG's storage
+// for PG != void the accumulation gacc(x) <- g(x) gacc(x) in PG's storage.
+// Registers are capped so that three blocks fit on an SM (the mapping the
+// single-lattice autotuner picks for the bandwidth-bound FP32 sweep).
 template <class P, class PG>
-__global__ void __launch_bounds__(kSweepTile) k_b_halfsweep(const BProb *probs, const int *tile_prob, int colour,
+__global__ void __launch_bounds__(kSweepTile, 3) k_b_halfsweep(const BProb *probs, const int *tile_prob, int colour,
                                                             int want_phase, double omega, int variant)
 {
     typedef typename P::Real T;
