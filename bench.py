@@ -50,6 +50,7 @@ BATCHED = {
     "gribov_su3_16x16x16x16_64copies_uneven": [((16, 16, 16, 16), 64), ((8, 8, 8, 8), 8), ((12, 12, 12, 12), 8),
                                                ((32, 16, 16, 16), 8), ((24, 24, 24, 24), 8)],
     "coulomb_su3_48x48x48x96": None,
+    "su3_64x64x64x64": None,
 }
 
 # algorithmic bytes per site update: 8 links read + 8 written
@@ -272,6 +273,65 @@ def run_profile_step(args):
         h.culgt_store(d_out)
         torch.cuda.synchronize()
     print(json.dumps({"profile_step": args.profile_step, "workload": args.workload, **out}), flush=True)
+    return 0
+
+
+def run_large_lattice(args):
+    """SU(3) 64^4 (eps 0.25, seed 3, omega 1.75): 200 timed sweeps in FP64
+    18-real and in FP32 12-real, then whole fixes to theta < 1e-12, mixed
+    FP32 -> FP64 and plain FP64."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1412_3655_gb300 import culgt, synth
+    dims, nc, eps, seed, omega = (64, 64, 64, 64), 3, 0.25, 3, 1.75
+    V = int(np.prod(dims))
+    U = synth.gauge_config(dims, nc, eps, seed)
+    d_in = torch.from_numpy(U.view(np.float64).copy()).cuda()
+    del U
+    d_out = torch.empty_like(d_in)
+    stream = torch.cuda.current_stream()
+    peaks, _ = measured_peaks()
+    out = {}
+    for name, prec, bps in [("fp64_18", culgt.FP64, 2304), ("fp32_12", culgt.FP32, 768)]:
+        p = culgt.Params.defaults(nc, dims, omega=omega, precision=prec)
+        with culgt.Handle(p, stream) as h:
+            h.culgt_load(d_in)
+            h.culgt_handle_sweep(10)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.culgt_handle_sweep(200)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / 200
+            gbs = V * bps / (ms / 1e3) / 1e9
+            out[name] = {"ms_per_sweep": ms, "site_updates_per_s": V / (ms / 1e3), "GB_per_s": gbs,
+                         "hbm_frac": gbs / float(peaks["hbm_gbs"]), "mapping": h.culgt_handle_tuning()}
+    fixes = {}
+    for name, prec in [("mixed", culgt.MIXED), ("fp64", culgt.FP64)]:
+        p = culgt.Params.defaults(nc, dims, omega=omega, precision=prec, check_every=10, reunit_every=50,
+                                  max_sweeps=40000)
+        with culgt.Handle(p, stream) as h:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.culgt_load(d_in)
+            r = h.culgt_handle_fix()
+            h.culgt_store(d_out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            fixes[name] = {"s": a.elapsed_time(b) / 1e3, "sweeps": [r.sweeps_fp32, r.sweeps_fp64], "theta": r.theta,
+                           "F": r.F, "status": r.status}
+    updates = sum(fixes["mixed"]["sweeps"]) * V
+    line = {
+        "metric": METRIC, "value": updates / fixes["mixed"]["s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+        "warmup": 0, "ms_per_step": 1e3 * fixes["mixed"]["s"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32->f64 (mixed)", "data": "synthetic",
+        "config": {"workload": args.workload, "dims": list(dims), "eps": eps, "seed": seed, "omega": omega},
+        "timed_sweeps_200": out, "time_to_theta": fixes,
+    }
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -553,6 +613,8 @@ def main():
         return run_reference(args)
     if args.profile_step:
         return run_profile_step(args)
+    if args.workload == "su3_64x64x64x64":
+        return run_large_lattice(args)
     if args.workload in BATCHED:
         return run_batched_workload(args)
     return run_culgt(args)

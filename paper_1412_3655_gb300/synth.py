@@ -214,19 +214,105 @@ def _links_for_sites(L, nc, eps, seed, copy, g, h, start, stop):
     return out
 
 
+def _shm_array(name, shape):
+    from multiprocessing import shared_memory
+    shm = shared_memory.SharedMemory(name=name)
+    return shm, np.ndarray(shape, dtype=np.complex128, buffer=shm.buf)
+
+
+def _gauge_chunk(args):
+    """worker: g (and h) of the sites [a, b) into shared memory"""
+    g_name, h_name, V, nc, L, seed, copy, spread, a, b = args
+    shm_g, g = _shm_array(g_name, (V, nc, nc))
+    shm_h, h = _shm_array(h_name, (V, nc, nc)) if h_name else (None, None)
+    try:
+        ga, ha = _gauge_at(np.arange(a, b, dtype=np.int64), L, nc, seed, copy, spread)
+        g[a:b] = ga
+        if h is not None:
+            h[a:b] = ha
+    finally:
+        shm_g.close()
+        if shm_h:
+            shm_h.close()
+    return b - a
+
+
+def _links_chunk(args):
+    """worker: the links of the sites [a, b) into shared memory"""
+    u_name, g_name, h_name, V, nc, L, eps, seed, copy, a, b = args
+    shm_u, U = _shm_array(u_name, (V, 4, nc, nc))
+    shm_g, g = _shm_array(g_name, (V, nc, nc))
+    shm_h, h = _shm_array(h_name, (V, nc, nc)) if h_name else (None, None)
+    try:
+        U[a:b] = _links_for_sites(L, nc, eps, seed, copy, g, h, a, b)
+    finally:
+        shm_u.close()
+        shm_g.close()
+        if shm_h:
+            shm_h.close()
+    return b - a
+
+
+def _spawn_safe() -> bool:
+    """Spawned workers re-import the parent's __main__; that fails when it was
+    read from stdin or a path that no longer exists."""
+    import os
+    import sys
+    f = getattr(sys.modules.get("__main__"), "__file__", None)
+    return f is None or os.path.exists(f)
+
+
+def _parallel_config(L, nc, eps, seed, copy, spread, workers):
+    from concurrent.futures import ProcessPoolExecutor
+    from multiprocessing import get_context, shared_memory
+    V = int(np.prod(L))
+    step = -(-V // (4 * workers))
+    chunks = [(a, min(V, a + step)) for a in range(0, V, step)]
+    shms = []
+    try:
+        su = shared_memory.SharedMemory(create=True, size=V * 4 * nc * nc * 16)
+        shms.append(su)
+        sg = shared_memory.SharedMemory(create=True, size=V * nc * nc * 16)
+        shms.append(sg)
+        sh = None
+        if copy:
+            sh = shared_memory.SharedMemory(create=True, size=V * nc * nc * 16)
+            shms.append(sh)
+        hn = sh.name if sh else None
+        with ProcessPoolExecutor(max_workers=workers, mp_context=get_context("spawn")) as ex:
+            list(ex.map(_gauge_chunk, [(sg.name, hn, V, nc, L, seed, copy, spread, a, b) for a, b in chunks]))
+            list(ex.map(_links_chunk, [(su.name, sg.name, hn, V, nc, L, eps, seed, copy, a, b) for a, b in chunks]))
+        return np.ndarray((V, 4, nc, nc), dtype=np.complex128, buffer=su.buf).copy()
+    finally:
+        for m in shms:
+            m.close()
+            m.unlink()
+
+
 def gauge_config(L, nc: int, eps: float, seed: int, copy: int = 0, chunk: int = 1 << 18,
-                 spread: float | None = None) -> np.ndarray:
+                 spread: float | None = None, workers: int | None = None) -> np.ndarray:
     """U_mu(x) = g(x) exp(i eps H_mu(x)) g(x+mu)^+ with Haar g, as (V, 4, Nc, Nc) complex128.
 
     copy > 0 returns the same configuration under a further Haar-random gauge
     transformation (an independent starting point on the same gauge orbit).
     spread replaces the Haar g by g = exp(i spread H(x)), a gauge close to 1.
     Every site is computed from its own counters, so the result does not
-    depend on chunk (the number of sites done at once)."""
+    depend on how the sites are split: lattices of 2^20 sites and more are
+    generated by `workers` spawned processes (default: the CPU count, at most
+    16) writing into shared memory, in chunks of `chunk` sites otherwise."""
+    import os
     L = tuple(int(v) for v in L)
     if len(L) != 4 or any(v < 2 for v in L):
         raise ValueError("dims must be four extents >= 2")
     V = int(np.prod(L))
+    if workers is None:
+        workers = min(os.cpu_count() or 1, 16) if V >= (1 << 20) else 1
+    if workers > 1 and _spawn_safe():
+        from concurrent.futures.process import BrokenProcessPool
+        try:
+            return _parallel_config(L, nc, eps, seed, copy, spread, workers)
+        except BrokenProcessPool:
+            pass  # a worker could not start: generate here instead
     U = np.empty((V, 4, nc, nc), dtype=np.complex128)
     g, h = _gauge_at(np.arange(V, dtype=np.int64), L, nc, seed, copy, spread)
     for start in range(0, V, chunk):
