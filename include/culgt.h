@@ -51,7 +51,7 @@ typedef enum {
     CULGT_ERR_CUDA = -4,      /* a CUDA runtime call failed */
     CULGT_ERR_OOM = -5,       /* device allocation failed */
     CULGT_ERR_NONFINITE = -6, /* theta or F came out NaN/Inf (corrupt links) */
-    CULGT_ERR_TIMEOUT = -7,   /* a bounded device-side wait gave up */
+    CULGT_ERR_TIMEOUT = -7,   /* reserved: no kernel of this library waits on another */
     CULGT_ERR_TOO_LARGE = -8  /* lattice larger than culgt_theta_static_scratch's fixed scratch */
 } culgt_status;
 

@@ -475,7 +475,7 @@ const char *culgt_status_string(int status)
     case CULGT_ERR_CUDA: return "CULGT_ERR_CUDA: a CUDA runtime call failed";
     case CULGT_ERR_OOM: return "CULGT_ERR_OOM: device allocation failed";
     case CULGT_ERR_NONFINITE: return "CULGT_ERR_NONFINITE: theta or F is not finite";
-    case CULGT_ERR_TIMEOUT: return "CULGT_ERR_TIMEOUT: a bounded device-side wait gave up";
+    case CULGT_ERR_TIMEOUT: return "CULGT_ERR_TIMEOUT: reserved (no device-side waits in this library)";
     case CULGT_ERR_TOO_LARGE:
         return "CULGT_ERR_TOO_LARGE: lattice above the 4,194,304 sites culgt_theta_static_scratch supports";
     default: return "unknown culgt status";
@@ -655,10 +655,8 @@ culgt_status culgt_handle_to_fp64(culgt_handle *h)
     CallScope scope(h);
     if (!h->cur32) return CULGT_OK;
     if (!h->ops64) return CULGT_ERR_ARG;  // an FP32-only handle has no FP64 buffer
-    if (h->gacc)
-        launch_rotate_orbit(h->ops32, h->gacc, h->ops64, h->buf64, h->geom, h->stream);
-    else
-        launch_widen(h->ops32, h->buf32, h->ops64, h->buf64, h->geom, h->stream);
+    if (!h->gacc) return CULGT_ERR_ARG;  // every mixed handle keeps the accumulator
+    launch_rotate_orbit(h->ops32, h->gacc, h->ops64, h->buf64, h->geom, h->stream);
     CU(cudaGetLastError());
     h->cur32 = 0;
     return CULGT_OK;

@@ -570,8 +570,7 @@ __global__ void __launch_bounds__(256) k_to_canonical(const typename P::Chunk *b
 }
 
 // ---------------------------------------------------------------------------
-// K5: precision switch FP32 -> FP64, one thread per (parity, mu, site): the
-// stored rows are widened and the link reunitarised in FP64 (row 2 rebuilt).
+// link conversions for the FP32 -> FP64 switch
 
 template <typename T> __device__ __forceinline__ void convert_link(const M3<double> &a, M3<T> &b)
 {
@@ -594,41 +593,6 @@ template <typename T> __device__ __forceinline__ void convert_link(const Q4<doub
 template <class P> struct Link64 {
     typedef typename std::conditional<P::NC == 3, M3<double>, Q4<double>>::type type;
 };
-
-template <class PIn, class POut>
-__global__ void __launch_bounds__(256) k_widen(const typename PIn::Chunk *src, typename POut::Chunk *dst, Geom g)
-{
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 8LL * g.Vh) return;
-    int plane = (int)(t / g.Vh);
-    int cb = (int)(t - (long long)plane * g.Vh);
-    typename PIn::Link a;
-    PIn::load_raw(src + (size_t)plane * PIn::NCHUNK * g.stride + cb, g.stride, a);
-    typename Link64<PIn>::type b;
-    if constexpr (PIn::NC == 3) {
-#pragma unroll
-        for (int r = 0; r < 2; r++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                b.re[r][c] = (double)a.re[r][c];
-                b.im[r][c] = (double)a.im[r][c];
-            }
-        m3_reunitarize(b);
-    } else {
-        double n = 0.0;
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            b.a[k] = (double)a.a[k];
-            n += b.a[k] * b.a[k];
-        }
-        n = 1.0 / sqrt(n);
-#pragma unroll
-        for (int k = 0; k < 4; k++) b.a[k] *= n;
-    }
-    typename POut::Link c;
-    convert_link(b, c);
-    POut::store(dst + (size_t)plane * POut::NCHUNK * g.stride + cb, g.stride, c);
-}
 
 // ---------------------------------------------------------------------------
 // Orbit-exact mixed precision. During the FP32 phase each site also keeps

@@ -57,9 +57,6 @@ long long launches_so_far();
 // nullptr if the combination is not built
 const Ops *get_ops(int nc, int fp32, int nreal);
 
-// FP32 links (any storage) -> FP64 links (18 reals for SU(3)), reunitarised in FP64
-void launch_widen(const Ops *from, const void *src, const Ops *to, void *dst, const Geom &g, cudaStream_t s);
-
 // FP64 links <- g(x) U g(x+mu)^+ with g from the FP32 accumulator of `from`
 void launch_rotate_orbit(const Ops *from, const void *gacc, const Ops *to, void *base64, const Geom &g,
                          cudaStream_t s);

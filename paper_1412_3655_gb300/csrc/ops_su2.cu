@@ -1,30 +1,11 @@
-// SU(2) links stored as quaternions, FP64 and FP32, and the FP32 -> FP64
-// precision switch for every parameterisation.
+// SU(2) links stored as quaternions, FP64 and FP32, and the orbit-exact
+// FP32 -> FP64 (or double-float) switch of the mixed schedule.
 #include "ops_impl.cuh"
 
 namespace culgt {
 const Ops ops_su2_d4 = OpsImpl<Param<2, double, 4>>::make();
 const Ops ops_su2_f4 = OpsImpl<Param<2, float, 4>>::make();
 
-void launch_widen(const Ops *from, const void *src, const Ops *to, void *dst, const Geom &g, cudaStream_t s)
-{
-    unsigned nb = blocks_for(8LL * g.Vh, 256);
-    if (from->nc == 3 && to->df && from->nreal == 12)
-        k_widen<Param<3, float, 12>, Param<3, dfl, 18>><<<nb, 256, 0, s>>>((const float4 *)src, (float4 *)dst, g);
-    else if (from->nc == 3 && to->df)
-        k_widen<Param<3, float, 18>, Param<3, dfl, 18>><<<nb, 256, 0, s>>>((const float2 *)src, (float4 *)dst, g);
-    else if (from->nc == 3 && from->nreal == 12 && to->nreal == 18)
-        k_widen<Param<3, float, 12>, Param<3, double, 18>>
-            <<<nb, 256, 0, s>>>((const float4 *)src, (double2 *)dst, g);
-    else if (from->nc == 3 && from->nreal == 18 && to->nreal == 18)
-        k_widen<Param<3, float, 18>, Param<3, double, 18>>
-            <<<nb, 256, 0, s>>>((const float2 *)src, (double2 *)dst, g);
-    else if (from->nc == 2 && to->df)
-        k_widen<Param<2, float, 4>, Param<2, dfl, 4>><<<nb, 256, 0, s>>>((const float4 *)src, (float4 *)dst, g);
-    else if (from->nc == 2)
-        k_widen<Param<2, float, 4>, Param<2, double, 4>><<<nb, 256, 0, s>>>((const float4 *)src, (double2 *)dst, g);
-    count_launch();
-}
 void launch_rotate_orbit(const Ops *from, const void *gacc, const Ops *to, void *base64, const Geom &g,
                          cudaStream_t s)
 {

@@ -384,3 +384,25 @@ def test_autotuner_picks_a_valid_mapping(cu):
             h.culgt_load(to_dev(U))
             tps, block, minb = h.culgt_handle_tuning()
             assert tps in (1, 2) and block in (64, 128, 256) and minb in (1, 3, 4)
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_checkpoint_and_resume(cu, nc):
+    """culgt_store is the checkpoint and culgt_load the resume: a fix stopped
+    at 50 sweeps, written to the canonical buffer and continued in a new
+    handle ends bit for bit where the uninterrupted fix ends (FP64-18 and the
+    canonical layout round-trip exactly; 50 is a multiple of the theta and
+    reunitarisation cadences)."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_config(dims, nc, 0.3, 1)
+    p = cu.Params.defaults(nc, dims, check_every=10, reunit_every=50, max_sweeps=2000)
+    whole = to_dev(U)
+    rw = cu.culgt_landau_fix(whole, p)
+    part = to_dev(U)
+    first = cu.Params(**{**p.__dict__, "max_sweeps": 50})
+    r1 = cu.culgt_landau_fix(part, first)
+    assert r1.status == cu.NOT_CONVERGED and r1.sweeps_fp64 == 50
+    rest = cu.Params(**{**p.__dict__, "max_sweeps": 2000 - 50})
+    r2 = cu.culgt_landau_fix(part, rest)
+    assert r2.sweeps_fp64 + 50 == rw.sweeps_fp64
+    assert torch.equal(part, whole)
