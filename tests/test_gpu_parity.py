@@ -389,20 +389,21 @@ def test_autotuner_picks_a_valid_mapping(cu):
 @pytest.mark.parametrize("nc", [2, 3])
 def test_checkpoint_and_resume(cu, nc):
     """culgt_store is the checkpoint and culgt_load the resume: a fix stopped
-    at 50 sweeps, written to the canonical buffer and continued in a new
+    at 20 sweeps, written to the canonical buffer and continued in a new
     handle ends bit for bit where the uninterrupted fix ends (FP64-18 and the
-    canonical layout round-trip exactly; 50 is a multiple of the theta and
+    canonical layout round-trip exactly; 20 is a multiple of the theta and
     reunitarisation cadences)."""
     dims = (4, 4, 4, 4)
     U = synth.gauge_config(dims, nc, 0.3, 1)
-    p = cu.Params.defaults(nc, dims, check_every=10, reunit_every=50, max_sweeps=2000)
+    p = cu.Params.defaults(nc, dims, check_every=10, reunit_every=20, max_sweeps=2000)
     whole = to_dev(U)
     rw = cu.culgt_landau_fix(whole, p)
+    assert rw.sweeps_fp64 > 20
     part = to_dev(U)
-    first = cu.Params(**{**p.__dict__, "max_sweeps": 50})
+    first = cu.Params(**{**p.__dict__, "max_sweeps": 20})
     r1 = cu.culgt_landau_fix(part, first)
-    assert r1.status == cu.NOT_CONVERGED and r1.sweeps_fp64 == 50
-    rest = cu.Params(**{**p.__dict__, "max_sweeps": 2000 - 50})
+    assert r1.status == cu.NOT_CONVERGED and r1.sweeps_fp64 == 20
+    rest = cu.Params(**{**p.__dict__, "max_sweeps": 2000 - 20})
     r2 = cu.culgt_landau_fix(part, rest)
-    assert r2.sweeps_fp64 + 50 == rw.sweeps_fp64
+    assert r2.sweeps_fp64 + 20 == rw.sweeps_fp64
     assert torch.equal(part, whole)
