@@ -175,6 +175,15 @@ culgt_status culgt_landau_fix_host(void *h_links, const culgt_params *p, void *c
 culgt_status culgt_coulomb_fix(void *d_links, const culgt_params *p, void *cuda_stream, culgt_result *per_slice,
                                void *d_gauge);
 
+/* Landau gauge fixing like culgt_landau_fix, also returning the gauge
+ * transformation: on return d_links = g(x) U_mu(x) g(x+mu)^+ for the input
+ * U and d_gauge = g(x) as [V][Nc][Nc] complex double (canonical site order),
+ * e.g. to rotate quark fields or propagators the same way. g is accumulated
+ * per site in the precision of each phase (FP32 accumulator in the FP32
+ * phase, FP64 or double-float afterwards) and reunitarised with the links. */
+culgt_status culgt_landau_fix_gauge(void *d_links, const culgt_params *p, void *cuda_stream, culgt_result *out,
+                                    void *d_gauge);
+
 /* n_sweeps sweeps of d_links in place at the given precision. */
 culgt_status culgt_sweep(void *d_links, const culgt_params *p, int n_sweeps, void *cuda_stream);
 

@@ -43,6 +43,7 @@ struct Lattice {
 struct Engine {
     culgt_params cp;
     bool coulomb = false;
+    bool want_gauge = false;  // keep g(x) in every phase so that it can be returned
     bool has32 = false, has64 = false, acc32 = false, acc64 = false;
     const Ops *o32 = nullptr, *o64 = nullptr;
     const BPhaseOps *b32 = nullptr, *b64 = nullptr;
@@ -99,8 +100,8 @@ struct Engine {
         }
         if ((has32 && (!o32 || !b32)) || (has64 && (!o64 || !b64))) return CULGT_ERR_NC;
         // accumulators: the mixed FP32 phase (orbit-exact switch) and Coulomb (temporal links)
-        acc32 = has32 && (has64 || coulomb);
-        acc64 = has64 && coulomb;
+        acc32 = has32 && (has64 || coulomb || want_gauge);
+        acc64 = has64 && (coulomb || want_gauge);
         rule.theta_target = p->theta_target;
         rule.fp32_target = mixed ? p->switch_theta : p->theta_target;
         rule.fp32_next = mixed ? PH_SWITCH : PH_DONE;
@@ -426,6 +427,49 @@ extern "C" culgt_status culgt_fix_batched(const culgt_problem *problems, int n, 
             out[i].unitarity_err = ue[i];
             out[i].seconds = secs;
         }
+    return e.status();
+}
+
+extern "C" culgt_status culgt_landau_fix_gauge(void *d_links, const culgt_params *p, void *cuda_stream,
+                                               culgt_result *out, void *d_gauge)
+{
+    double t0 = wall_now();
+    culgt_status st = culgt_validate(p);
+    if (st != CULGT_OK) return st;
+    if (!d_links || !d_gauge) return CULGT_ERR_ARG;
+    if (cudaStreamSynchronize((cudaStream_t)cuda_stream) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return CULGT_ERR_CUDA;
+    }
+    Engine e;
+    e.want_gauge = true;
+    EST(e.init(p));
+    EST(e.add_lattice(p->dims, d_links));
+    e.add_problem(e.lat[0], 0, e.lat[0].g.Vh, 0, 0);
+    EST(e.alloc_lattice_partials());
+    EST(e.upload());
+    double pb, pa, ue;
+    EST(e.plaquette(e.lat[0], &pb));
+    EST(e.run());
+    EST(e.plaquette(e.lat[0], &pa));
+    EST(e.unitarity(e.lat[0], &ue));
+    const Lattice &L = e.lat[0];
+    const BPhaseOps *b = e.has64 ? e.b64 : e.b32;
+    const void *acc = e.has64 ? L.gacc64 : L.gacc32;
+    launch_gauge_to_canonical(p->nc, b->fp32 ? 1 : (e.o64->df ? 2 : 0), acc, (double *)d_gauge, L.g, e.s);
+    if (cudaGetLastError() != cudaSuccess) return CULGT_ERR_CUDA;
+    EST(e.store_all());
+    if (out) {
+        const BProb &r = e.hp[0];
+        out->sweeps_fp32 = r.sweeps32;
+        out->sweeps_fp64 = r.sweeps64;
+        out->theta = r.theta;
+        out->F = r.F;
+        out->plaq_before = pb;
+        out->plaq_after = pa;
+        out->unitarity_err = ue;
+        out->seconds = wall_now() - t0;
+    }
     return e.status();
 }
 

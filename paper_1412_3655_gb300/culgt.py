@@ -154,6 +154,7 @@ def library():
         "culgt_plaquette": (ip, [vp, P, vp, dp]),
         "culgt_theta_static_scratch": (ip, [vp, P, vp, vp]),
         "culgt_coulomb_fix": (ip, [vp, P, vp, R, vp]),
+        "culgt_landau_fix_gauge": (ip, [vp, P, vp, R, vp]),
         "culgt_fix_batched": (ip, [ctypes.POINTER(_Problem), ip, P, vp, R]),
         "culgt_reunitarize": (ip, [vp, P, vp]),
     }
@@ -239,23 +240,35 @@ def culgt_landau_fix_host(links, params: Params, stream=None) -> Result:
     return Result._from(r, st)
 
 
+def _gauge_ptr(gauge, params: Params):
+    import torch
+    V = 1
+    for d in params.dims:
+        V *= int(d)
+    real = torch.view_as_real(gauge) if gauge.is_complex() else gauge
+    if not (gauge.is_cuda and real.dtype == torch.float64 and gauge.is_contiguous()
+            and real.numel() == V * params.nc * params.nc * 2):
+        raise ValueError("gauge must be a contiguous CUDA float64 tensor of V*Nc*Nc*2 reals")
+    return ctypes.c_void_p(gauge.data_ptr())
+
+
+def culgt_landau_fix_gauge(links, params: Params, gauge, stream=None) -> Result:
+    """Landau gauge fixing in place that also writes g(x) into `gauge`
+    (CUDA float64/complex128 tensor of V * Nc * Nc complex values)."""
+    r = _Result()
+    st = _check(library().culgt_landau_fix_gauge(_links_ptr(links, params, True), ctypes.byref(params._c()),
+                                                 _stream(stream), ctypes.byref(r), _gauge_ptr(gauge, params)),
+                "culgt_landau_fix_gauge")
+    return Result._from(r, st)
+
+
 def culgt_coulomb_fix(links, params: Params, stream=None, gauge=None):
     """Coulomb gauge fixing in place, one problem per time slice. Returns one
     Result per slice (status on each). gauge: optional CUDA float64 tensor of
     V * Nc * Nc * 2 elements that receives g(x)."""
     nt = int(params.dims[0])
     rs = (_Result * nt)()
-    gp = None
-    if gauge is not None:
-        import torch
-        V = 1
-        for d in params.dims:
-            V *= int(d)
-        real = torch.view_as_real(gauge) if gauge.is_complex() else gauge
-        if not (gauge.is_cuda and real.dtype == torch.float64 and gauge.is_contiguous()
-                and real.numel() == V * params.nc * params.nc * 2):
-            raise ValueError("gauge must be a contiguous CUDA float64 tensor of V*Nc*Nc*2 reals")
-        gp = ctypes.c_void_p(gauge.data_ptr())
+    gp = _gauge_ptr(gauge, params) if gauge is not None else None
     st = _check(library().culgt_coulomb_fix(_links_ptr(links, params, True), ctypes.byref(params._c()),
                                             _stream(stream), rs, gp), "culgt_coulomb_fix")
     return [Result._from(r, st) for r in rs]

@@ -143,3 +143,26 @@ def test_batched_max_sweeps_and_status(cu):
     res = cu.culgt_fix_batched([to_dev(U) for U in Us], [dims, (2, 2, 2, 2)], p)
     assert res[0].status == cu.NOT_CONVERGED
     assert [r.sweeps_fp64 for r in res] == [7, 7]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_df"])
+@pytest.mark.parametrize("nc", [2, 3])
+def test_landau_fix_returns_the_gauge_transformation(cu, orc, nc, precision):
+    """culgt_landau_fix_gauge: the output is the input transformed by the
+    returned g (to the accuracy of the accumulation), and converges like the
+    FP64 oracle."""
+    prec = {"fp64": cu.FP64, "mixed": cu.MIXED, "mixed_df": cu.MIXED_DF}[precision]
+    dims = (4, 4, 4, 4)
+    V = int(np.prod(dims))
+    U = synth.gauge_config(dims, nc, 0.3, 1)
+    d = to_dev(U)
+    gauge = torch.zeros(V * nc * nc * 2, dtype=torch.float64, device="cuda")
+    p = cu.Params.defaults(nc, dims, precision=prec, check_every=5, reunit_every=50, max_sweeps=3000)
+    r = cu.culgt_landau_fix_gauge(d, p, gauge)
+    rr = orc.landau_fix(U.copy(), dims, nc, 1.7, 1e-12, 3000, 1)
+    assert r.status == cu.OK and r.theta < 1e-12
+    assert r.F == pytest.approx(rr["F"], rel=1e-10)
+    g = gauge.cpu().numpy().view(np.complex128).reshape(V, nc, nc)
+    assert np.abs(g @ np.swapaxes(g.conj(), 1, 2) - np.eye(nc)).max() < 1e-13
+    tol = 1e-12 if prec == cu.FP64 else 1e-10
+    assert np.abs(from_dev(d, U.shape) - synth.gauge_transform(U, dims, g)).max() < tol
