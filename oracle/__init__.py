@@ -2,7 +2,9 @@
 
 A thin ctypes binding over ``culgt_oracle.c``: a plain, slow restatement of
 lattice Landau/Coulomb gauge fixing as defined in Vogt & Schröck, "cuLGT:
-Lattice Gauge Fixing on GPUs", Sec. 2. Only the tests, ``__graft_entry__.smoke``
+Lattice Gauge Fixing on GPUs", Sec. 2, and of the simulated annealing the paper
+combines with it (heat bath over the SU(2) subgroups, readings R7-R11 in
+``culgt_oracle.c``). Only the tests, ``__graft_entry__.smoke``
 and the CPU-baseline leg of ``bench.py`` use this module; the CUDA library never
 does, and the two share no code.
 
@@ -45,6 +47,7 @@ def _load():
     dp = ctypes.POINTER(ctypes.c_double)
     ip = ctypes.POINTER(ctypes.c_int)
     i, d = ctypes.c_int, ctypes.c_double
+    u32p = ctypes.POINTER(ctypes.c_uint32)
     sig = {
         "oracle_halfsweep": (None, [dp, ip, i, i, d, i]),
         "oracle_sweep": (None, [dp, ip, i, d, i, i]),
@@ -58,6 +61,14 @@ def _load():
         "oracle_local_gauge": (None, [dp, i, d, i, dp]),
         "oracle_su2_local_max": (None, [dp, dp]),
         "oracle_overrelax": (None, [dp, d, i, dp]),
+        "oracle_philox4x32_10": (None, [u32p, u32p, u32p]),
+        "oracle_hb_delta": (d, [d, u32p, ctypes.c_uint32, ctypes.c_uint32, i, ip]),
+        "oracle_hb_x": (None, [d, u32p, ctypes.c_uint32, ctypes.c_uint32, i, dp]),
+        "oracle_heatbath_gauge": (None, [dp, i, d, u32p, ctypes.c_uint32, ctypes.c_uint32, dp]),
+        "oracle_heatbath_halfsweep": (None, [dp, ip, i, i, d, u32p, ctypes.c_uint32, dp]),
+        "oracle_heatbath_sweep": (None, [dp, ip, i, d, u32p, ctypes.c_uint32, dp]),
+        "oracle_micro_sweep": (None, [dp, ip, i]),
+        "oracle_anneal": (None, [dp, ip, i, d, d, i, i, u32p, i]),
         "oracle_set_threads": (None, [i]),
         "oracle_get_threads": (i, []),
     }
@@ -187,3 +198,73 @@ def overrelax(g, omega, variant=0):
     out = np.zeros((2, 2), dtype=np.complex128)
     _load().oracle_overrelax(_dp(g), float(omega), int(variant), _dp(out))
     return out
+
+
+# --- simulated annealing (readings R7-R11 of culgt_oracle.c) ---
+
+def _key(seed: int):
+    """The Philox key of a 64-bit seed: (low word, high word)."""
+    seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    return (ctypes.c_uint32 * 2)(seed & 0xFFFFFFFF, seed >> 32)
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 of one counter (4 words) and key (2 words); returns 4 words."""
+    c = (ctypes.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    out = (ctypes.c_uint32 * 4)()
+    _load().oracle_philox4x32_10(c, k, out)
+    return tuple(int(x) for x in out)
+
+
+def hb_delta(alpha, seed, site, sweep, sub=0):
+    """(delta, attempts): delta = 1 - x0 of one heat-bath draw at alpha = 2 k / T."""
+    n = ctypes.c_int()
+    dlt = _load().oracle_hb_delta(float(alpha), _key(seed), int(site), int(sweep), int(sub), ctypes.byref(n))
+    return float(dlt), n.value
+
+
+def hb_x(alpha, seed, site, sweep, sub=0):
+    """The unit quaternion (x0, x1, x2, x3) of one heat-bath draw."""
+    x = np.zeros(4)
+    _load().oracle_hb_x(float(alpha), _key(seed), int(site), int(sweep), int(sub), _dp(x))
+    return x
+
+
+def heatbath_gauge(K, T, seed, site, sweep):
+    """The heat-bath transformation g of one site with gathered K (Nc x Nc)."""
+    K = np.ascontiguousarray(K, dtype=np.complex128)
+    nc = K.shape[0]
+    g = np.zeros((nc, nc), dtype=np.complex128)
+    _load().oracle_heatbath_gauge(_dp(K), nc, float(T), _key(seed), int(site), int(sweep), _dp(g))
+    return g
+
+
+def heatbath_sweep(U, L, nc, T, seed, sweep, gacc=None):
+    """One heat-bath sweep at temperature T (draw counter word `sweep`), in place.
+    gacc (V, Nc, Nc) complex128, if given, accumulates g(x) gacc(x)."""
+    _check_links(U, L, nc)
+    g = None
+    if gacc is not None:
+        assert gacc.dtype == np.complex128 and gacc.flags["C_CONTIGUOUS"]
+        g = _dp(gacc)
+    _load().oracle_heatbath_sweep(_dp(U), _dims(L), nc, float(T), _key(seed), int(sweep), g)
+
+
+def heatbath_halfsweep(U, L, nc, parity, T, seed, sweep):
+    """Heat-bath update of every site of one parity (0 = black), in place."""
+    _check_links(U, L, nc)
+    _load().oracle_heatbath_halfsweep(_dp(U), _dims(L), nc, int(parity), float(T), _key(seed), int(sweep), None)
+
+
+def micro_sweep(U, L, nc):
+    """One microcanonical (omega = 2) sweep, in place."""
+    _check_links(U, L, nc)
+    _load().oracle_micro_sweep(_dp(U), _dims(L), nc)
+
+
+def anneal(U, L, nc, t_start, t_end, steps, n_micro, seed, reunit_every=0):
+    """The annealing schedule of R11, in place (no overrelaxation afterwards)."""
+    _check_links(U, L, nc)
+    _load().oracle_anneal(_dp(U), _dims(L), nc, float(t_start), float(t_end), int(steps), int(n_micro),
+                          _key(seed), int(reunit_every))

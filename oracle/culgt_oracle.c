@@ -36,9 +36,21 @@
  *   R6  Coulomb: each time slice is an independent 3D Landau problem over
  *       mu = 1..3 with its own checkerboard (black = x1+x2+x3 even); the
  *       accumulated g(x) rotates the temporal links once at the end.
+ *   R7  Simulated annealing (named, not specified, by the paper) replaces the
+ *       maximisation of each SU(2) subgroup (R1) by a heat-bath draw from
+ *       exp(Re tr[r w] / T) over SU(2) at temperature T.
+ *   R8  Uniforms come from the top 24 bits of a Philox4x32-10 word.
+ *   R9  Draw counters: (site, heat-bath sweep, (attempt << 4) | (subgroup << 1)
+ *       | kind, 0), keyed by the 64-bit seed.
+ *   R10 x0 = 1 - delta by Creutz's method below alpha = 2, by Kennedy and
+ *       Pendleton's above; at most 32 attempts, then delta = 0.
+ *   R11 Schedule: T linear from t_start to t_end over `steps` heat-bath
+ *       sweeps, each followed by n_micro microcanonical sweeps (omega = 2);
+ *       reunitarisation counts sweeps of both kinds.
  */
 #include <math.h>
 #include <stddef.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
@@ -670,6 +682,241 @@ int oracle_coulomb_fix(double *U, const int *L, int nc, double omega, int varian
 }
 
 /* ------------------------------------------------------------------ */
+/* simulated annealing (the paper's abstract and Sec. 1; R7-R11)       */
+/* ------------------------------------------------------------------ */
+
+/* Philox4x32-10 (Salmon, Moraes, Dror and Shaw, "Parallel random numbers:
+ * as easy as 1, 2, 3", SC 2011): ten rounds, each mapping the counter
+ * (c0, c1, c2, c3) with the key (k0, k1) to
+ *   (hi(B c2) ^ c1 ^ k0, lo(B c2), hi(A c0) ^ c3 ^ k1, lo(A c0)),
+ * A = 0xD2511F53, B = 0xCD9E8D57 (32 x 32 -> 64-bit products), and adding
+ * the Weyl increments 0x9E3779B9, 0xBB67AE85 to the key between rounds. */
+void oracle_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out)
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t pa = (uint64_t)0xD2511F53u * c0;
+        uint64_t pb = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t n0 = (uint32_t)(pb >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)pb;
+        uint32_t n2 = (uint32_t)(pa >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)pa;
+        c0 = n0;
+        c1 = n1;
+        c2 = n2;
+        c3 = n3;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+/* R8: a uniform in (0, 1) from the top 24 bits of a word, (w/256 + 1/2) 2^-24;
+ * every value is exact in float and in double. */
+static double unit_uniform(uint32_t w) { return ((double)(w >> 8) + 0.5) * (1.0 / 16777216.0); }
+
+/* R9: the counter of a draw: (canonical site index, heat-bath sweep index,
+ * (attempt << 4) | (subgroup << 1) | kind, 0); kind 0 = the attempt's four
+ * uniforms for x0, kind 1 = the direction. Subgroups count 0, 1, 2 in the
+ * order of R1 (0 for SU(2)). */
+static void draw4(const uint32_t *key, uint32_t site, uint32_t sweep, uint32_t word2, double u[4])
+{
+    uint32_t ctr[4] = {site, sweep, word2, 0u};
+    uint32_t w[4];
+    oracle_philox4x32_10(ctr, key, w);
+    for (int k = 0; k < 4; k++) u[k] = unit_uniform(w[k]);
+}
+
+#define HB_CREUTZ_BELOW 2.0
+static const double TWO_PI = 6.283185307179586;
+#define HB_MAX_ATTEMPTS 32
+
+/* R10: delta = 1 - x0 for an SU(2) element x whose x0 has the density
+ * proportional to sqrt(1 - x0^2) exp(alpha x0) on [-1, 1] (the heat-bath
+ * distribution of the subgroup at temperature T, alpha = 2 k / T, see below).
+ * alpha < 2: Creutz's method, x0 drawn from exp(alpha x0) by inverting its
+ * distribution function, kept with probability sqrt(1 - x0^2).
+ * alpha >= 2: Kennedy and Pendleton's, delta drawn from Gamma(3/2, alpha)
+ * as -(log u0 + cos^2(2 pi u1) log u2) / alpha, kept with probability
+ * sqrt(1 - delta/2). With 1 - x0^2 = delta (2 - delta) both tests compare
+ * squares. After HB_MAX_ATTEMPTS rejections (below 1e-16 at any alpha) the
+ * draw gives delta = 0. *attempts receives the number of attempts made. */
+double oracle_hb_delta(double alpha, const uint32_t *key, uint32_t site, uint32_t sweep, int sub, int *attempts)
+{
+    for (int a = 0; a < HB_MAX_ATTEMPTS; a++) {
+        double u[4];
+        draw4(key, site, sweep, ((uint32_t)a << 4) | ((uint32_t)sub << 1), u);
+        if (attempts) *attempts = a + 1;
+        if (alpha < HB_CREUTZ_BELOW) {
+            double delta = -log1p(u[0] * expm1(-2.0 * alpha)) / alpha;
+            if (u[1] * u[1] <= delta * (2.0 - delta)) return delta;
+        } else {
+            double c = cos(TWO_PI * u[1]);
+            double delta = -(log(u[0]) + c * c * log(u[2])) / alpha;
+            if (u[3] * u[3] <= 1.0 - 0.5 * delta) return delta;
+        }
+    }
+    return 0.0;
+}
+
+/* The unit quaternion x = (1 - delta, s n) with s = sqrt(delta (2 - delta))
+ * and n uniform on the sphere: cos(theta) = 2 u0 - 1, phi = 2 pi u1. */
+void oracle_hb_x(double alpha, const uint32_t *key, uint32_t site, uint32_t sweep, int sub, double *x)
+{
+    double delta = oracle_hb_delta(alpha, key, site, sweep, sub, NULL);
+    double u[4];
+    draw4(key, site, sweep, ((uint32_t)sub << 1) | 1u, u);
+    double ct = 2.0 * u[0] - 1.0;
+    double st = sqrt(1.0 - ct * ct);
+    double phi = TWO_PI * u[1];
+    double s = sqrt(delta * (2.0 - delta));
+    x[0] = 1.0 - delta;
+    x[1] = s * st * cos(phi);
+    x[2] = s * st * sin(phi);
+    x[3] = s * ct;
+}
+
+/* the 2x2 matrix x0 1 + i (x1 s1 + x2 s2 + x3 s3) */
+static mat quaternion_matrix(const double *x)
+{
+    mat X = mat_zero(2);
+    X.m[0][0] = c_make(x[0], x[3]);
+    X.m[0][1] = c_make(x[2], x[1]);
+    X.m[1][0] = c_make(-x[2], x[1]);
+    X.m[1][1] = c_make(x[0], -x[3]);
+    return X;
+}
+
+/* Heat bath for one 2x2 block w at temperature T (R7): with q = P(w) = k v^+,
+ * k = sqrt(det q) and v = q^+/k the maximiser of Re tr[r w], every r = x v
+ * has Re tr[r w] = Re tr[x v q] = k Re tr[x] = 2 k x0, so the Boltzmann
+ * weight exp(Re tr[r w] / T) over Haar measure is that of x0 above with
+ * alpha = 2 k / T and a uniform direction. r = x v, rescaled to det r = 1.
+ * k = 0 leaves the block alone (as R4). */
+static mat heatbath_su2(const mat *w, double inv_T, const uint32_t *key, uint32_t site, uint32_t sweep, int sub)
+{
+    mat q = su2_part(w);
+    double k = sqrt(mat_det2(&q).re);
+    if (!(k > 0.0)) return mat_identity(2);
+    mat v = su2_local_max(w);
+    double x[4];
+    oracle_hb_x((2.0 * k) * inv_T, key, site, sweep, sub, x);
+    mat X = quaternion_matrix(x);
+    mat r = mat_mul(&X, &v);
+    cplx s = c_sqrt(mat_det2(&r));
+    mat out = mat_zero(2);
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++) out.m[a][b] = c_div(r.m[a][b], s);
+    return out;
+}
+
+/* The heat-bath gauge transformation of one site: SU(2) directly, SU(3)
+ * over the subgroups of R1 with the running K, as in local_gauge. */
+static mat heatbath_gauge(const mat *K, double inv_T, const uint32_t *key, uint32_t site, uint32_t sweep)
+{
+    int n = K->n;
+    if (n == 2) return heatbath_su2(K, inv_T, key, site, sweep, 0);
+    static const int sub[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    mat Kr = *K;
+    mat g = mat_identity(3);
+    for (int s = 0; s < 3; s++) {
+        int i = sub[s][0], j = sub[s][1];
+        mat w = mat_zero(2);
+        w.m[0][0] = Kr.m[i][i];
+        w.m[0][1] = Kr.m[i][j];
+        w.m[1][0] = Kr.m[j][i];
+        w.m[1][1] = Kr.m[j][j];
+        mat r = heatbath_su2(&w, inv_T, key, site, sweep, s);
+        mat R = mat_identity(3);
+        R.m[i][i] = r.m[0][0];
+        R.m[i][j] = r.m[0][1];
+        R.m[j][i] = r.m[1][0];
+        R.m[j][j] = r.m[1][1];
+        Kr = mat_mul(&R, &Kr);
+        g = mat_mul(&R, &g);
+    }
+    return g;
+}
+
+static void heatbath_site(double *U, const lattice *lat, int nc, long i, double inv_T, const uint32_t *key,
+                          uint32_t sweep, double *gacc)
+{
+    mat K = gather_K(U, lat, nc, i, 0);
+    mat g = heatbath_gauge(&K, inv_T, key, (uint32_t)i, sweep);
+    mat gd = mat_adj(&g);
+    for (int mu = 0; mu < 4; mu++) {
+        long ib = site_shift(lat, i, mu, -1);
+        mat f = get_link(U, nc, i, mu);
+        mat b = get_link(U, nc, ib, mu);
+        mat fn = mat_mul(&g, &f);
+        mat bn = mat_mul(&b, &gd);
+        put_link(U, nc, i, mu, &fn);
+        put_link(U, nc, ib, mu, &bn);
+    }
+    if (gacc) {
+        mat a = get_mat(gacc, nc, i);
+        mat an = mat_mul(&g, &a);
+        put_mat(gacc, nc, i, &an);
+    }
+}
+
+/* One heat-bath sweep at temperature T (black, then white; Landau, mu =
+ * 0..3); `sweep` is the counter word of its draws. gacc (V Nc Nc complex, or
+ * NULL) accumulates g(x) <- g(x) gacc(x). */
+void oracle_heatbath_halfsweep(double *U, const int *L, int nc, int parity, double T, const uint32_t *key,
+                               uint32_t sweep, double *gacc)
+{
+    lattice lat = make_lattice(L);
+    double inv_T = 1.0 / T;
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < lat.V; i++)
+        if (site_parity(&lat, i, 0) == parity) heatbath_site(U, &lat, nc, i, inv_T, key, sweep, gacc);
+}
+
+void oracle_heatbath_sweep(double *U, const int *L, int nc, double T, const uint32_t *key, uint32_t sweep,
+                           double *gacc)
+{
+    oracle_heatbath_halfsweep(U, L, nc, 0, T, key, sweep, gacc);
+    oracle_heatbath_halfsweep(U, L, nc, 1, T, key, sweep, gacc);
+}
+
+/* Microcanonical sweep: overrelaxation at omega = 2, r -> r^2 for the
+ * maximiser r of every subgroup, which keeps each local functional (R11). */
+void oracle_micro_sweep(double *U, const int *L, int nc)
+{
+    oracle_sweep(U, L, nc, 2.0, 0, 1);
+}
+
+/* R11: the annealing schedule. Step k = 0..steps-1 runs one heat-bath sweep
+ * at T_k = t_start + (t_end - t_start) k / (steps - 1) (T_0 = t_start for
+ * steps = 1) with counter word `sweep` = k, then n_micro microcanonical
+ * sweeps. Counting every sweep of either kind, the links are reunitarised
+ * after each reunit_every-th (reunit_every > 0). */
+void oracle_anneal(double *U, const int *L, int nc, double t_start, double t_end, int steps, int n_micro,
+                   const uint32_t *key, int reunit_every)
+{
+    lattice lat = make_lattice(L);
+    long done = 0;
+    for (int k = 0; k < steps; k++) {
+        double T = steps > 1 ? t_start + (t_end - t_start) * (double)k / (double)(steps - 1) : t_start;
+        for (int m = 0; m <= n_micro; m++) {
+            if (m == 0)
+                oracle_heatbath_sweep(U, L, nc, T, key, (uint32_t)k, NULL);
+            else
+                oracle_micro_sweep(U, L, nc);
+            done++;
+            if (reunit_every > 0 && done % reunit_every == 0) oracle_reunitarize(U, lat.V * 4, nc);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* single-matrix entry points for the pin tests                        */
 /* ------------------------------------------------------------------ */
 
@@ -687,6 +934,16 @@ void oracle_su2_local_max(const double *w, double *r)
     mat a = get_mat(w, 2, 0);
     mat b = su2_local_max(&a);
     put_mat(r, 2, 0, &b);
+}
+
+/* the heat-bath transformation of one site for a gathered K at temperature T,
+ * drawn with counter words (site, sweep) */
+void oracle_heatbath_gauge(const double *K, int nc, double T, const uint32_t *key, uint32_t site, uint32_t sweep,
+                           double *g)
+{
+    mat k = get_mat(K, nc, 0);
+    mat r = heatbath_gauge(&k, 1.0 / T, key, site, sweep);
+    put_mat(g, nc, 0, &r);
 }
 
 /* g^omega for one SU(2) matrix */
