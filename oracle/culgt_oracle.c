@@ -39,7 +39,7 @@
  *   R7  Simulated annealing (named, not specified, by the paper) replaces the
  *       maximisation of each SU(2) subgroup (R1) by a heat-bath draw from
  *       exp(Re tr[r w] / T) over SU(2) at temperature T.
- *   R8  Uniforms come from the top 24 bits of a Philox4x32-10 word.
+ *   R8  Uniforms come from the top 23 bits of a Philox4x32-10 word.
  *   R9  Draw counters: (site, heat-bath sweep, (attempt << 4) | (subgroup << 1)
  *       | kind, 0), keyed by the 64-bit seed.
  *   R10 x0 = 1 - delta by Creutz's method below alpha = 2, by Kennedy and
@@ -717,9 +717,9 @@ void oracle_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *ou
     out[3] = c3;
 }
 
-/* R8: a uniform in (0, 1) from the top 24 bits of a word, (w/256 + 1/2) 2^-24;
- * every value is exact in float and in double. */
-static double unit_uniform(uint32_t w) { return ((double)(w >> 8) + 0.5) * (1.0 / 16777216.0); }
+/* R8: a uniform in (0, 1) from the top 23 bits m of a word, (m + 1/2) 2^-23:
+ * odd multiples of 2^-24, every one exact in float and in double. */
+static double unit_uniform(uint32_t w) { return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 /* R9: the counter of a draw: (canonical site index, heat-bath sweep index,
  * (attempt << 4) | (subgroup << 1) | kind, 0); kind 0 = the attempt's four
