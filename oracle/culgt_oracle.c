@@ -43,7 +43,8 @@
  *   R9  Draw counters: (site, heat-bath sweep, (attempt << 4) | (subgroup << 1)
  *       | kind, 0), keyed by the 64-bit seed.
  *   R10 x0 = 1 - delta by Creutz's method below alpha = 2, by Kennedy and
- *       Pendleton's above; at most 32 attempts, then delta = 0.
+ *       Pendleton's above; at most 32 attempts, then delta = 0. 1 - x0^2 is
+ *       formed as (1 - x0)(1 + x0) from two separately accurate factors.
  *   R11 Schedule: T linear from t_start to t_end over `steps` heat-bath
  *       sweeps, each followed by n_micro microcanonical sweeps (omega = 2);
  *       reunitarisation counts sweeps of both kinds.
@@ -737,45 +738,68 @@ static void draw4(const uint32_t *key, uint32_t site, uint32_t sweep, uint32_t w
 static const double TWO_PI = 6.283185307179586;
 #define HB_MAX_ATTEMPTS 32
 
-/* R10: delta = 1 - x0 for an SU(2) element x whose x0 has the density
- * proportional to sqrt(1 - x0^2) exp(alpha x0) on [-1, 1] (the heat-bath
- * distribution of the subgroup at temperature T, alpha = 2 k / T, see below).
- * alpha < 2: Creutz's method, x0 drawn from exp(alpha x0) by inverting its
- * distribution function, kept with probability sqrt(1 - x0^2).
- * alpha >= 2: Kennedy and Pendleton's, delta drawn from Gamma(3/2, alpha)
- * as -(log u0 + cos^2(2 pi u1) log u2) / alpha, kept with probability
- * sqrt(1 - delta/2). With 1 - x0^2 = delta (2 - delta) both tests compare
- * squares. After HB_MAX_ATTEMPTS rejections (below 1e-16 at any alpha) the
- * draw gives delta = 0. *attempts receives the number of attempts made. */
-double oracle_hb_delta(double alpha, const uint32_t *key, uint32_t site, uint32_t sweep, int sub, int *attempts)
+/* R10: delta = 1 - x0 and eps = 1 + x0 for an SU(2) element x whose x0 has
+ * the density proportional to sqrt(1 - x0^2) exp(alpha x0) on [-1, 1] (the
+ * heat-bath distribution of the subgroup at temperature T, alpha = 2 k / T,
+ * see below). alpha < 2: Creutz's method, x0 drawn from exp(alpha x0) by
+ * inverting its distribution function, kept with probability
+ * sqrt(1 - x0^2); the inversion gives delta and eps each from its own
+ * logarithm, so that both keep their relative accuracy near x0 = +1 and -1.
+ * alpha >= 2: Kennedy and Pendleton's, delta drawn from Gamma(3/2, alpha) as
+ * -(log u0 + cos^2(2 pi u1) log u2) / alpha, kept with probability
+ * sqrt(1 - delta/2), and eps = 2 - delta. Both tests compare squares, with
+ * 1 - x0^2 = delta eps. After HB_MAX_ATTEMPTS rejections (below 1e-16 at any
+ * alpha) the draw gives delta = 0, eps = 2. *attempts receives the number of
+ * attempts made. */
+static void hb_draw(double alpha, const uint32_t *key, uint32_t site, uint32_t sweep, int sub, double *delta,
+                    double *eps, int *attempts)
 {
     for (int a = 0; a < HB_MAX_ATTEMPTS; a++) {
         double u[4];
         draw4(key, site, sweep, ((uint32_t)a << 4) | ((uint32_t)sub << 1), u);
         if (attempts) *attempts = a + 1;
         if (alpha < HB_CREUTZ_BELOW) {
-            double delta = -log1p(u[0] * expm1(-2.0 * alpha)) / alpha;
-            if (u[1] * u[1] <= delta * (2.0 - delta)) return delta;
+            double d = -log1p(u[0] * expm1(-2.0 * alpha)) / alpha;
+            double e = log1p((1.0 - u[0]) * expm1(2.0 * alpha)) / alpha;
+            if (u[1] * u[1] <= d * e) {
+                *delta = d;
+                *eps = e;
+                return;
+            }
         } else {
             double c = cos(TWO_PI * u[1]);
-            double delta = -(log(u[0]) + c * c * log(u[2])) / alpha;
-            if (u[3] * u[3] <= 1.0 - 0.5 * delta) return delta;
+            double d = -(log(u[0]) + c * c * log(u[2])) / alpha;
+            if (u[3] * u[3] <= 1.0 - 0.5 * d) {
+                *delta = d;
+                *eps = 2.0 - d;
+                return;
+            }
         }
     }
-    return 0.0;
+    *delta = 0.0;
+    *eps = 2.0;
 }
 
-/* The unit quaternion x = (1 - delta, s n) with s = sqrt(delta (2 - delta))
- * and n uniform on the sphere: cos(theta) = 2 u0 - 1, phi = 2 pi u1. */
+double oracle_hb_delta(double alpha, const uint32_t *key, uint32_t site, uint32_t sweep, int sub, int *attempts)
+{
+    double d, e;
+    hb_draw(alpha, key, site, sweep, sub, &d, &e, attempts);
+    return d;
+}
+
+/* The unit quaternion x = (1 - delta, s n) with s = sqrt(delta eps) and n
+ * uniform on the sphere: cos(theta) = 2 u0 - 1, sin(theta) = 2 sqrt(u0 (1 - u0)),
+ * phi = 2 pi u1. */
 void oracle_hb_x(double alpha, const uint32_t *key, uint32_t site, uint32_t sweep, int sub, double *x)
 {
-    double delta = oracle_hb_delta(alpha, key, site, sweep, sub, NULL);
+    double delta, eps;
+    hb_draw(alpha, key, site, sweep, sub, &delta, &eps, NULL);
     double u[4];
     draw4(key, site, sweep, ((uint32_t)sub << 1) | 1u, u);
     double ct = 2.0 * u[0] - 1.0;
-    double st = sqrt(1.0 - ct * ct);
+    double st = 2.0 * sqrt(u[0] * (1.0 - u[0]));
     double phi = TWO_PI * u[1];
-    double s = sqrt(delta * (2.0 - delta));
+    double s = sqrt(delta * eps);
     x[0] = 1.0 - delta;
     x[1] = s * st * cos(phi);
     x[2] = s * st * sin(phi);
