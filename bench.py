@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--profile-step", choices=["mixed", "fp64", "fp32", "df", "mixed_df"], default=None,
                     help="run one gauge fixing (or --profile-sweeps sweeps) of the workload and exit; "
                          "the command the ncu captures in profiles/ wrap")
+    ap.add_argument("--profile-heatbath", type=float, default=0.0,
+                    help="with --profile-step and --profile-sweeps: heat-bath sweeps at this temperature instead")
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="with --profile-step: this many sweeps instead of a whole fix")
     ap.add_argument("--tps", type=int, default=0, help="with --profile-step: threads per site (0 = autotune)")
@@ -115,7 +117,7 @@ def measured_peaks():
 
 # files that define the single-lattice sweep kernels: a recorded ncu traffic
 # figure holds only while these are unchanged
-KERNEL_SOURCES = ("culgt_device.cuh", "dfloat.cuh", "kernels.cuh", "ops_impl.cuh")
+KERNEL_SOURCES = ("culgt_device.cuh", "dfloat.cuh", "kernels.cuh", "ops_impl.cuh", "anneal.cuh")
 
 
 def source_hash():
@@ -276,7 +278,12 @@ def run_profile_step(args):
                               min_blocks_per_sm=args.minb)
     with culgt.Handle(p) as h:
         h.culgt_load(d_in)
-        if args.profile_sweeps:
+        if args.profile_sweeps and args.profile_heatbath > 0:
+            for k in range(args.profile_sweeps):
+                h.culgt_handle_heatbath(args.profile_heatbath, 1, k)
+            th, F = h.culgt_handle_theta()
+            out = {"heatbath_sweeps": args.profile_sweeps, "T": args.profile_heatbath, "theta": th, "F": F}
+        elif args.profile_sweeps:
             h.culgt_handle_sweep(args.profile_sweeps)
             th, F = h.culgt_handle_theta()
             out = {"sweeps": args.profile_sweeps, "theta": th, "F": F}
@@ -398,6 +405,54 @@ def run_batched_workload(args):
     run(culgt.MIXED)  # warm-up (autotuning, graph capture)
     t_mixed, r_mixed, per = run(culgt.MIXED)
     t_fp64, r_fp64, _ = run(culgt.FP64)
+    anneal = None
+    if args.workload.startswith("gribov"):
+        # simulated annealing before the overrelaxation (the paper's combination
+        # for the Gribov-copy search); copy j draws with seed + j
+        a = culgt.culgt_default_anneal_params()
+        a.seed = 11
+        ds = [t.to(dev) for t in inputs]
+        p = culgt.Params.defaults(nc, dims_list[0], omega=omega, precision=culgt.MIXED, check_every=10,
+                                  reunit_every=50, max_sweeps=20000)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r_ann = culgt.culgt_fix_batched_anneal(ds, dims_list, p, a)
+        torch.cuda.synchronize()
+        t_ann = time.perf_counter() - t0
+        best_plain, best_ann = {}, {}
+        for g, r0, r1 in zip(groups, r_mixed, r_ann):
+            best_plain[g] = max(best_plain.get(g, -1.0), r0.F)
+            best_ann[g] = max(best_ann.get(g, -1.0), r1.F)
+        sa_sweeps = a.steps * (1 + a.micro_sweeps)
+        anneal = {
+            "schedule": {"t_start": a.t_start, "t_end": a.t_end, "steps": a.steps, "micro_sweeps": a.micro_sweeps,
+                         "seed": a.seed},
+            "s": t_ann, "all_converged": all(r.status == culgt.OK for r in r_ann),
+            "site_updates_per_s": sum((sa_sweeps + r.sweeps_fp32 + r.sweeps_fp64) * n
+                                      for r, n in zip(r_ann, per)) / t_ann,
+            "mean_F": float(np.mean([r.F for r in r_ann])), "mean_F_without": float(np.mean([r.F for r in r_mixed])),
+            "max_F": best_ann, "max_F_without": best_plain,
+            "copies_above_without": float(np.mean([r1.F > r0.F + 1e-12 for r0, r1 in zip(r_mixed, r_ann)])),
+        }
+        # a rougher field (eps 0.6), where overrelaxation alone ends on
+        # different local maxima from different copies
+        rough_dims = (8, 8, 8, 8)
+        rough = [torch.from_numpy(synth.gauge_config(rough_dims, nc, 0.6, 4, copy=c).view(np.float64).copy())
+                 for c in range(32)]
+        pr = culgt.Params.defaults(nc, rough_dims, omega=omega, precision=culgt.MIXED, check_every=10,
+                                   reunit_every=50, max_sweeps=50000)
+        r0 = culgt.culgt_fix_batched([t.to(dev) for t in rough], [rough_dims] * 32, pr)
+        t0 = time.perf_counter()
+        r1 = culgt.culgt_fix_batched_anneal([t.to(dev) for t in rough], [rough_dims] * 32, pr, a)
+        torch.cuda.synchronize()
+        anneal["rough_field"] = {
+            "workload": "32 gauge copies of one 8^4 SU(3) field, eps 0.6", "s": time.perf_counter() - t0,
+            "all_converged": all(r.status == culgt.OK for r in r0 + r1),
+            "mean_F": float(np.mean([r.F for r in r1])), "mean_F_without": float(np.mean([r.F for r in r0])),
+            "max_F": max(r.F for r in r1), "max_F_without": max(r.F for r in r0),
+            "distinct_maxima_without": len({round(r.F, 9) for r in r0}),
+            "distinct_maxima": len({round(r.F, 9) for r in r1}),
+        }
     updates = sum((r.sweeps_fp32 + r.sweeps_fp64) * n for r, n in zip(r_mixed, per))
     maxF = {}
     for g, r in zip(groups, r_mixed):
@@ -420,6 +475,8 @@ def run_batched_workload(args):
         "mixed_vs_fp64_max_dF": max(abs(a.F - b.F) for a, b in zip(r_mixed, r_fp64)),
         "plaquette_drift_max": max(abs(r.plaq_after - r.plaq_before) for r in r_mixed),
     }
+    if anneal:
+        line["anneal"] = anneal
     print(json.dumps(line), flush=True)
     return 0
 
@@ -535,6 +592,23 @@ def run_culgt(args):
                 "hbm_frac": (V // 2) * BYTES_PER_SITE[key] / (t_ms / 1e3) / 1e9 / hbm,
                 "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (unit counts and max clock)"}
 
+    # heat-bath (simulated annealing) half-sweeps: one thread per site, blocks of 128
+    def heatbath_ms(params, n_sweeps=20):
+        with culgt.Handle(params, stream) as hk:
+            hk.culgt_load(d_in)
+            hk.culgt_handle_heatbath(0.5, 1, 0)
+            keep, minb = hk.culgt_handle_heatbath_tuning()
+            mapping["heatbath_" + ("fp32_phase" if params.precision == culgt.MIXED else "fp64")] = (keep, 128, minb)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for k in range(n_sweeps):
+                hk.culgt_handle_heatbath(0.5, 1, k + 1)
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / (2 * n_sweeps)
+
+    thb32 = heatbath_ms(mixed)
+    thb64 = heatbath_ms(plain, 10)
     rl32 = roofline_hbm((nc, 1, 12 if nc == 3 else 4, "acc"), t32, mapping["fp32_phase"])
     rl64 = roofline_fp64((nc, 0, 18 if nc == 3 else 4), t64, mapping["fp64"])
     dominant = rl32 if share32 >= share64 else rl64
@@ -563,6 +637,15 @@ def run_culgt(args):
     rldf = roofline_hbm((nc, 0, 18 if nc == 3 else 4), tdf, mapping["double_float"])
     rldf["kernel"] = rldf["kernel"].replace("f64", "df")
     rldf["traffic"] = recorded_traffic(rldf["kernel"])
+    mk = mapping["heatbath_fp32_phase"]
+    rlhb32 = roofline_hbm((nc, 1, 12 if nc == 3 else 4, "acc"), thb32, mk)
+    rlhb32["kernel"] = rlhb32["kernel"].replace("halfsweep", "heatbath").replace(f"_tps{mk[0]}_", f"_keep{mk[0]}_")
+    rlhb32["traffic"] = recorded_traffic(rlhb32["kernel"])
+    mk = mapping["heatbath_fp64"]
+    rlhb64 = roofline_fp64((nc, 0, 18 if nc == 3 else 4), thb64, mk)
+    rlhb64["kernel"] = rlhb64["kernel"].replace("halfsweep", "heatbath").replace(f"_tps{mk[0]}_", f"_keep{mk[0]}_")
+    rlhb64["traffic"] = recorded_traffic(rlhb64["kernel"])
+    rlhb64["note"] = "flops counted as for the overrelaxation update; the draw adds its own"
     # the FP32 -> FP64 switch later: the orbit-exact switch keeps the FP32
     # rounding off the result, so the FP32 phase may run to a lower theta
     late = {}
@@ -602,9 +685,12 @@ def run_culgt(args):
                                   "double-float sweeps (float pairs, ~48-bit) with theta/F in FP64; "
                                   "mixed_switch_later: the same schedule with the FP32 phase run to a lower theta"},
         "roofline": dominant,
-        "roofline_kernels": {"fp32_phase": rl32, "fp64": rl64, "double_float": rldf},
+        "roofline_kernels": {"fp32_phase": rl32, "fp64": rl64, "double_float": rldf,
+                             "heatbath_fp32_phase": rlhb32, "heatbath_fp64": rlhb64},
         "gpu_launches": launches,
-        "sweep_mapping": {k: {"threads_per_site": v[0], "block": v[1], "min_blocks_per_sm": v[2]}
+        "sweep_mapping": {k: ({"keep_links": v[0], "block": v[1], "min_blocks_per_sm": v[2]} if
+                              k.startswith("heatbath") else
+                              {"threads_per_site": v[0], "block": v[1], "min_blocks_per_sm": v[2]})
                           for k, v in mapping.items()},
         "e2e": {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": canon_bytes,
                 "d2h_bytes_per_step": canon_bytes, "steps": n_e2e},

@@ -230,6 +230,65 @@ typedef struct {
 culgt_status culgt_fix_batched(const culgt_problem *problems, int n, const culgt_params *common, void *cuda_stream,
                                culgt_result *out);
 
+/* ---- simulated annealing ------------------------------------------------
+ * The paper combines overrelaxation with simulated annealing to aim for the
+ * global maximum of F among the local maxima (Gribov copies) of a gauge
+ * orbit (abstract, Sec. 1), without printing the method; this is our
+ * reading of it. A heat-bath sweep is the checkerboard sweep of Sec. 2 with
+ * the maximisation of every SU(2) subgroup replaced by a draw from the
+ * weight exp(Re tr[r w] / T) over SU(2) at temperature T (x0 by Creutz's
+ * method below alpha = 2 k / T = 2, by Kennedy and Pendleton's above). A
+ * microcanonical sweep is overrelaxation at omega = 2, which moves the links
+ * along the orbit without changing F. Draws come from Philox4x32-10 keyed by
+ * the 64-bit seed, with the counter (canonical site index, sweep word,
+ * (attempt << 4) | (subgroup << 1) | kind, 0): the draws of a lattice depend
+ * on nothing else (not on the thread mapping or on the batch it is in). */
+typedef struct {
+    double t_start;          /* temperature of the first heat-bath sweep, finite and > 0 */
+    double t_end;            /* temperature of the last, finite and > 0 */
+    int steps;               /* heat-bath sweeps, >= 0 */
+    int micro_sweeps;        /* microcanonical sweeps after each heat-bath sweep, >= 0 */
+    unsigned long long seed; /* Philox key (low word, high word) */
+} culgt_anneal_params;
+
+/* Defaults for the synthetic fields of the tests (t_start 0.6, t_end 0.01,
+ * 500 steps, 3 microcanonical sweeps, seed 0); the paper gives no schedule,
+ * tune it per ensemble. */
+culgt_status culgt_default_anneal_params(culgt_anneal_params *out);
+culgt_status culgt_validate_anneal(const culgt_anneal_params *a);
+
+/* One heat-bath sweep (black, then white) of a loaded handle at temperature
+ * T > 0, drawing with the given seed and sweep word. In the FP32 phase of a
+ * mixed handle it also accumulates g(x), like an overrelaxation sweep. */
+culgt_status culgt_handle_heatbath(culgt_handle *h, double T, unsigned long long seed, unsigned sweep_word);
+
+/* The heat-bath mapping the handle uses: whether the eight links stay in
+ * registers between gather and update, and the blocks of 128 per SM the
+ * registers are capped for. Chosen like the half-sweep mapping (timed on a
+ * scratch copy at the first heat-bath sweep for lattices of 65536 sites and
+ * more, cached per storage and volume); every mapping gives the same links. */
+culgt_status culgt_handle_heatbath_tuning(culgt_handle *h, int *keep_links, int *min_blocks_per_sm);
+
+/* The annealing schedule on a loaded handle: step k = 0 .. steps-1 is one
+ * heat-bath sweep at T_k = t_start + (t_end - t_start) k / (steps - 1)
+ * (T_0 = t_start when steps = 1) with sweep word k, then micro_sweeps
+ * microcanonical sweeps; counting the sweeps of both kinds, the links are
+ * reunitarised after every reunit_every-th. These sweeps are not counted in
+ * culgt_result. */
+culgt_status culgt_handle_anneal(culgt_handle *h, const culgt_anneal_params *a);
+
+/* Landau gauge fixing like culgt_landau_fix, with the annealing schedule run
+ * between the load and the overrelaxation. */
+culgt_status culgt_landau_fix_anneal(void *d_links, const culgt_params *p, const culgt_anneal_params *a,
+                                     void *cuda_stream, culgt_result *out);
+
+/* culgt_fix_batched with the annealing schedule run on every problem first
+ * (in shared launches, all problems in step). Problem j draws with the key
+ * seed + j, so its draws are those of culgt_landau_fix_anneal with that
+ * seed. */
+culgt_status culgt_fix_batched_anneal(const culgt_problem *problems, int n, const culgt_params *common,
+                                      const culgt_anneal_params *a, void *cuda_stream, culgt_result *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -46,6 +46,8 @@ struct culgt_handle {
     int sweeps32, sweeps64;
     // half-sweep mapping per precision: threads per site, block, blocks per SM (0 = not chosen yet)
     int tps32, block32, minb32, tps64, block64, minb64;
+    // heat-bath mapping per precision (variant + 1; 0 = not chosen yet)
+    int hb32, hb64;
 };
 
 namespace {
@@ -330,6 +332,135 @@ void reunitarize_now(culgt_handle *h)
     if (h->cur32 && h->gacc) h->ops32->gauge_reunitarize(h->gacc, h->geom, h->stream);
 }
 
+// ---- simulated annealing: heat-bath and microcanonical sweeps ----
+
+culgt_status validate_anneal(const culgt_anneal_params *a)
+{
+    if (!a) return CULGT_ERR_ARG;
+    if (!(a->t_start > 0.0) || !(a->t_end > 0.0) || std::isinf(a->t_start) || std::isinf(a->t_end))
+        return CULGT_ERR_ARG;
+    if (a->steps < 0 || a->micro_sweeps < 0) return CULGT_ERR_ARG;
+    return CULGT_OK;
+}
+
+// T_k of the schedule, linear in k from t_start to t_end
+double anneal_temperature(const culgt_anneal_params *a, int k)
+{
+    return a->steps > 1 ? a->t_start + (a->t_end - a->t_start) * (double)k / (double)(a->steps - 1) : a->t_start;
+}
+
+// The heat-bath mapping, timed like the half-sweep's (autotune): every
+// variant on a scratch copy, the fastest kept per (storage, volume,
+// accumulation) for the process; lattices below kTuneMinSites take variant 0.
+std::map<std::tuple<const Ops *, int, bool>, int> g_hb_cache;
+
+culgt_status tuned_heatbath(culgt_handle *h, int *variant)
+{
+    int *slot = h->cur32 ? &h->hb32 : &h->hb64;
+    if (*slot) {
+        *variant = *slot - 1;
+        return CULGT_OK;
+    }
+    const Ops *o = cur_ops(h);
+    const bool acc = h->cur32 && h->gacc;
+    int pick = 0;
+    if (o->heatbath_variants > 1 && h->geom.V >= kTuneMinSites) {
+        auto key = std::make_tuple(o, h->geom.V, acc);
+        bool cached = false;
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mutex);
+            auto it = g_hb_cache.find(key);
+            if (it != g_hb_cache.end()) {
+                pick = it->second;
+                cached = true;
+            }
+        }
+        if (!cached) {
+            size_t bytes = buffer_bytes(o, h->geom);
+            size_t gbytes = acc ? gauge_bytes(o, h->geom) : 0;
+            void *scratch = nullptr;
+            if (cudaMalloc(&scratch, bytes + gbytes) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return CULGT_ERR_OOM;
+            }
+            void *gscratch = acc ? (char *)scratch + bytes : nullptr;
+            CU(cudaMemcpyAsync(scratch, cur_buf(h), bytes, cudaMemcpyDeviceToDevice, h->stream));
+            if (acc) CU(cudaMemcpyAsync(gscratch, h->gacc, gbytes, cudaMemcpyDeviceToDevice, h->stream));
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            float best = 1e30f;
+            for (int v = 0; v < o->heatbath_variants; v++) {
+                o->heatbath(scratch, gscratch, h->geom, 0, 1.0, 0u, 0u, 0u, v, h->stream);
+                cudaEventRecord(e0, h->stream);
+                for (int r = 0; r < 2; r++)
+                    for (int parity = 0; parity < 2; parity++)
+                        o->heatbath(scratch, gscratch, h->geom, parity, 1.0, 0u, 0u, (unsigned)r, v, h->stream);
+                cudaEventRecord(e1, h->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                count_launch(-5);  // tuning launches are not part of the caller's work
+                if (ms < best) {
+                    best = ms;
+                    pick = v;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            cudaFree(scratch);
+            CU(cudaGetLastError());
+            std::lock_guard<std::mutex> lock(g_tune_mutex);
+            g_hb_cache[key] = pick;
+        }
+    }
+    *slot = pick + 1;
+    *variant = pick;
+    return CULGT_OK;
+}
+
+culgt_status heatbath_now(culgt_handle *h, double T, unsigned long long seed, unsigned sweep)
+{
+    int v;
+    ST(tuned_heatbath(h, &v));
+    const Ops *o = cur_ops(h);
+    void *acc = (h->cur32 && h->gacc) ? h->gacc : nullptr;
+    for (int parity = 0; parity < 2; parity++)
+        o->heatbath(cur_buf(h), acc, h->geom, parity, 1.0 / T, (uint32_t)seed, (uint32_t)(seed >> 32), sweep, v,
+                    h->stream);
+    return CULGT_OK;
+}
+
+// overrelaxation at omega = 2 (r -> r^2 per subgroup keeps Re tr[r w])
+culgt_status micro_now(culgt_handle *h)
+{
+    Mapping m;
+    ST(tuned_mapping(h, &m));
+    const Ops *o = cur_ops(h);
+    void *acc = (h->cur32 && h->gacc) ? h->gacc : nullptr;
+    for (int parity = 0; parity < 2; parity++)
+        o->halfsweep(cur_buf(h), acc, h->geom, parity, 2.0, 0, m.tps, m.block, m.minb, h->stream);
+    return CULGT_OK;
+}
+
+culgt_status anneal_now(culgt_handle *h, const culgt_anneal_params *a)
+{
+    long long done = 0;
+    for (int k = 0; k < a->steps; k++) {
+        const double T = anneal_temperature(a, k);
+        for (int m = 0; m <= a->micro_sweeps; m++) {
+            if (m == 0)
+                ST(heatbath_now(h, T, a->seed, (unsigned)k));
+            else
+                ST(micro_now(h));
+            done++;
+            if (h->prm.reunit_every > 0 && done % h->prm.reunit_every == 0) reunitarize_now(h);
+        }
+    }
+    CU(cudaGetLastError());
+    return CULGT_OK;
+}
+
 // One check interval: k sweeps (reunitarising after sweep n + j when due)
 // and the theta of the result, queued into h_scalars.
 culgt_status interval_enqueue(culgt_handle *h, int k, int n)
@@ -442,13 +573,15 @@ double now_seconds()
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// load, fix, diagnostics, store: the body of the one-call entry points
-culgt_status fix_call(culgt_handle *h, const void *d_in, void *d_out, culgt_result *out, double t0)
+// load, (anneal,) fix, diagnostics, store: the body of the one-call entry points
+culgt_status fix_call(culgt_handle *h, const void *d_in, void *d_out, culgt_result *out, double t0,
+                      const culgt_anneal_params *anneal = nullptr)
 {
     culgt_result r;
     std::memset(&r, 0, sizeof r);
     ST(culgt_load(h, d_in));
     ST(plaquette_now(h, &r.plaq_before, h->buf64 != nullptr));
+    if (anneal) ST(anneal_now(h, anneal));
     culgt_status st = fix_handle(h, &r);
     if (st < 0) return st;
     ST(plaquette_now(h, &r.plaq_after));
@@ -689,6 +822,59 @@ culgt_status culgt_landau_fix(void *d_links, const culgt_params *p, void *cuda_s
     HandleGuard g;
     ST(culgt_create(p, cuda_stream, &g.h));
     return fix_call(g.h, d_links, d_links, out, t0);
+}
+
+culgt_status culgt_default_anneal_params(culgt_anneal_params *out)
+{
+    if (!out) return CULGT_ERR_ARG;
+    std::memset(out, 0, sizeof *out);
+    out->t_start = 0.6;
+    out->t_end = 0.01;
+    out->steps = 500;
+    out->micro_sweeps = 3;
+    out->seed = 0;
+    return CULGT_OK;
+}
+
+culgt_status culgt_validate_anneal(const culgt_anneal_params *a) { return validate_anneal(a); }
+
+culgt_status culgt_handle_heatbath(culgt_handle *h, double T, unsigned long long seed, unsigned sweep_word)
+{
+    if (!h || !h->loaded || !(T > 0.0) || std::isinf(T)) return CULGT_ERR_ARG;
+    CallScope scope(h);
+    ST(heatbath_now(h, T, seed, sweep_word));
+    CU(cudaGetLastError());
+    return CULGT_OK;
+}
+
+culgt_status culgt_handle_heatbath_tuning(culgt_handle *h, int *keep_links, int *min_blocks_per_sm)
+{
+    if (!h || !h->loaded || !keep_links || !min_blocks_per_sm) return CULGT_ERR_ARG;
+    CallScope scope(h);
+    int v;
+    ST(tuned_heatbath(h, &v));
+    cur_ops(h)->heatbath_mapping(v, keep_links, min_blocks_per_sm);
+    return CULGT_OK;
+}
+
+culgt_status culgt_handle_anneal(culgt_handle *h, const culgt_anneal_params *a)
+{
+    if (!h || !h->loaded) return CULGT_ERR_ARG;
+    ST(validate_anneal(a));
+    CallScope scope(h);
+    return anneal_now(h, a);
+}
+
+culgt_status culgt_landau_fix_anneal(void *d_links, const culgt_params *p, const culgt_anneal_params *a,
+                                     void *cuda_stream, culgt_result *out)
+{
+    double t0 = now_seconds();
+    ST(validate(p));
+    ST(validate_anneal(a));
+    if (!d_links) return CULGT_ERR_ARG;
+    HandleGuard g;
+    ST(culgt_create(p, cuda_stream, &g.h));
+    return fix_call(g.h, d_links, d_links, out, t0, a);
 }
 
 culgt_status culgt_landau_fix_host(void *h_links, const culgt_params *p, void *cuda_stream, culgt_result *out)

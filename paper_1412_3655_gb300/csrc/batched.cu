@@ -305,6 +305,34 @@ struct Engine {
         return CULGT_OK;
     }
 
+    // the annealing schedule on every problem, all in the starting phase
+    // (FP32 for FP32 and mixed, accumulating g where that phase does)
+    culgt_status anneal(const culgt_anneal_params *a)
+    {
+        const int phase = has32 ? PH_FP32 : PH_FP64;
+        const BPhaseOps *b = has32 ? b32 : b64;
+        const bool acc = has32 ? acc32 : acc64;
+        long long done = 0;
+        for (int k = 0; k < a->steps; k++) {
+            const double T =
+                a->steps > 1 ? a->t_start + (a->t_end - a->t_start) * (double)k / (double)(a->steps - 1) : a->t_start;
+            for (int m = 0; m <= a->micro_sweeps; m++) {
+                for (int colour = 0; colour < 2; colour++) {
+                    if (m == 0)
+                        b->heatbath(dp, d_sweep_map, n_sweep_tiles, colour, phase, 1.0 / T, a->seed, (uint32_t)k, acc,
+                                    s);
+                    else
+                        b->sweep(dp, d_sweep_map, n_sweep_tiles, colour, phase, 2.0, 0, acc, s);
+                }
+                done++;
+                if (cp.reunit_every > 0 && done % cp.reunit_every == 0)
+                    b->reunit(dp, d_theta_map, n_theta_tiles, phase, acc, s);
+            }
+        }
+        BCU(cudaGetLastError());
+        return CULGT_OK;
+    }
+
     culgt_status plaquette(const Lattice &L, double *P)
     {
         const Ops *o = has64 ? o64 : o32;
@@ -381,11 +409,14 @@ struct Engine {
 
 } // namespace
 
-extern "C" culgt_status culgt_fix_batched(const culgt_problem *problems, int n, const culgt_params *common,
-                                          void *cuda_stream, culgt_result *out)
+namespace {
+
+culgt_status fix_batched(const culgt_problem *problems, int n, const culgt_params *common,
+                         const culgt_anneal_params *anneal, void *cuda_stream, culgt_result *out)
 {
     double t0 = wall_now();
     if (!problems || n <= 0 || !common) return CULGT_ERR_ARG;
+    if (anneal) EST(culgt_validate_anneal(anneal));
     for (int i = 0; i < n; i++) {
         culgt_params p = *common;
         for (int mu = 0; mu < 4; mu++) p.dims[mu] = problems[i].dims[mu];
@@ -408,6 +439,7 @@ extern "C" culgt_status culgt_fix_batched(const culgt_problem *problems, int n, 
     EST(e.upload());
     std::vector<double> pb(n), pa(n), ue(n);
     for (int i = 0; i < n; i++) EST(e.plaquette(e.lat[i], &pb[i]));
+    if (anneal) EST(e.anneal(anneal));
     EST(e.run());
     for (int i = 0; i < n; i++) {
         EST(e.plaquette(e.lat[i], &pa[i]));
@@ -428,6 +460,21 @@ extern "C" culgt_status culgt_fix_batched(const culgt_problem *problems, int n, 
             out[i].seconds = secs;
         }
     return e.status();
+}
+
+} // namespace
+
+extern "C" culgt_status culgt_fix_batched(const culgt_problem *problems, int n, const culgt_params *common,
+                                          void *cuda_stream, culgt_result *out)
+{
+    return fix_batched(problems, n, common, nullptr, cuda_stream, out);
+}
+
+extern "C" culgt_status culgt_fix_batched_anneal(const culgt_problem *problems, int n, const culgt_params *common,
+                                                 const culgt_anneal_params *a, void *cuda_stream, culgt_result *out)
+{
+    if (!a) return CULGT_ERR_ARG;
+    return fix_batched(problems, n, common, a, cuda_stream, out);
 }
 
 extern "C" culgt_status culgt_landau_fix_gauge(void *d_links, const culgt_params *p, void *cuda_stream,

@@ -12,7 +12,7 @@
 // check to know when every problem has retired.
 #pragma once
 
-#include "kernels.cuh"
+#include "anneal.cuh"
 
 namespace culgt {
 
@@ -49,27 +49,18 @@ struct BRule {
     int max_sweeps;
 };
 
-// site (cb, p) of a problem: the site update of Sec. 2 on its own links, and
-// for PG != void the accumulation gacc(x) <- g(x) gacc(x) in PG's storage.
-// Registers are capped so that three blocks fit on an SM (the mapping the
-// single-lattice autotuner picks for the bandwidth-bound FP32 sweep).
-template <class P, class PG>
-__global__ void __launch_bounds__(kSweepTile, 3) k_b_halfsweep(const BProb *probs, const int *tile_prob, int colour,
-                                                            int want_phase, double omega, int variant)
+// site (cb, p) of a problem: the site update of Sec. 2 with the given
+// subgroup step on the problem's links, and for PG != void the accumulation
+// gacc(x) <- g(x) gacc(x) in PG's storage.
+template <class P, class PG, bool KEEP = KeepLinks<P>::value, class Step>
+__device__ __forceinline__ void b_site_update(const BProb &pr, int cb, int p, int want_phase, const Step &step)
 {
     typedef typename P::Real T;
-    const int tile = blockIdx.x;
-    const BProb &pr = probs[tile_prob[tile]];
-    if (pr.phase != want_phase) return;
-    const int local = (tile - pr.sweep_tile0) * kSweepTile + threadIdx.x;
-    if (local >= pr.n_cb) return;
-    const int cb = pr.cb_begin + local;
-    const int p = (colour + pr.par_off) & 1;
     const Geom g = pr.g;
     typename P::Chunk *base = (typename P::Chunk *)(want_phase == PH_FP32 ? pr.links32 : pr.links64);
     if constexpr (P::NC == 3) {
         M3<T> G;
-        su3_site_update<P, KeepLinks<P>::value>(base, g, cb, p, pr.mu_first, (T)omega, variant, &G);
+        su3_update<P, KEEP, 1>(base, g, cb, p, 0, true, pr.mu_first, step, &G);
         if constexpr (!std::is_void<PG>::value) {
             typedef typename PG::Real A;
             typename PG::Chunk *gp = (typename PG::Chunk *)(want_phase == PH_FP32 ? pr.gacc32 : pr.gacc64) +
@@ -89,7 +80,7 @@ __global__ void __launch_bounds__(kSweepTile, 3) k_b_halfsweep(const BProb *prob
         }
     } else {
         Q4<T> G;
-        su2_site_update<P>(base, g, cb, p, pr.mu_first, (T)omega, variant, &G);
+        su2_update<P, 1>(base, g, cb, p, 0, true, pr.mu_first, step, &G);
         if constexpr (!std::is_void<PG>::value) {
             typedef typename PG::Real A;
             typename PG::Chunk *gp = (typename PG::Chunk *)(want_phase == PH_FP32 ? pr.gacc32 : pr.gacc64) +
@@ -99,6 +90,56 @@ __global__ void __launch_bounds__(kSweepTile, 3) k_b_halfsweep(const BProb *prob
             PG::store(gp, g.stride, q_mul(Ga, a));
         }
     }
+}
+
+// One colour of an overrelaxation half-sweep over every problem in
+// want_phase. Registers are capped so that three blocks fit on an SM (the
+// mapping the single-lattice autotuner picks for the bandwidth-bound FP32
+// sweep).
+template <class P, class PG>
+__global__ void __launch_bounds__(kSweepTile, 3) k_b_halfsweep(const BProb *probs, const int *tile_prob, int colour,
+                                                            int want_phase, double omega, int variant)
+{
+    const int tile = blockIdx.x;
+    const BProb &pr = probs[tile_prob[tile]];
+    if (pr.phase != want_phase) return;
+    const int local = (tile - pr.sweep_tile0) * kSweepTile + threadIdx.x;
+    if (local >= pr.n_cb) return;
+    const int cb = pr.cb_begin + local;
+    const int p = (colour + pr.par_off) & 1;
+    b_site_update<P, PG>(pr, cb, p, want_phase, OrStep<typename P::Real>{(typename P::Real)omega, variant});
+}
+
+// the batched heat-bath mapping: for FP32 SU(3) links re-read instead of
+// held, registers capped for four blocks per SM (the single-lattice tuner's
+// pick on a 32^4 lattice); otherwise the defaults
+template <class P> struct BHb {
+    static constexpr bool kFP32 = sizeof(typename P::Real) == 4;
+    static constexpr bool keep = (kFP32 && P::NC == 3) ? false : KeepLinks<P>::value;
+    static constexpr int minb = (kFP32 && P::NC == 3) ? 4 : 1;
+};
+
+// One colour of a heat-bath half-sweep (simulated annealing) at 1/T =
+// inv_temp over every problem in want_phase. Problem j draws with the key
+// seed + j, so its draws are those of a single-lattice call with that seed.
+template <class P, class PG>
+__global__ void __launch_bounds__(kSweepTile, BHb<P>::minb) k_b_heatbath(const BProb *probs, const int *tile_prob,
+                                                                        int colour, int want_phase, double inv_temp,
+                                                                        unsigned long long seed, uint32_t sweep)
+{
+    typedef typename P::Real T;
+    const int tile = blockIdx.x;
+    const int j = tile_prob[tile];
+    const BProb &pr = probs[j];
+    if (pr.phase != want_phase) return;
+    const int local = (tile - pr.sweep_tile0) * kSweepTile + threadIdx.x;
+    if (local >= pr.n_cb) return;
+    const int cb = pr.cb_begin + local;
+    const int p = (colour + pr.par_off) & 1;
+    const unsigned long long key = seed + (unsigned long long)j;
+    const HbStep<T> step{(T)(P::NC == 3 ? inv_temp : 2.0 * inv_temp), (uint32_t)key, (uint32_t)(key >> 32),
+                         canonical_site(pr.g, cb, p), sweep};
+    b_site_update<P, PG, BHb<P>::keep>(pr, cb, p, want_phase, step);
 }
 
 // the theta grid of a problem: s in [0, 2 n_cb) -> parity s / n_cb, cb in the problem's range

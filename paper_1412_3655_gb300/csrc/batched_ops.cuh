@@ -13,6 +13,9 @@ struct BPhaseOps {
     // one colour of a half-sweep over every problem in `phase`; acc: also accumulate g
     void (*sweep)(const BProb *probs, const int *map, int ntiles, int colour, int phase, double omega, int variant,
                   bool acc, cudaStream_t s);
+    // one colour of a heat-bath half-sweep at 1/T = inv_temp (problem j keyed by seed + j)
+    void (*heatbath)(const BProb *probs, const int *map, int ntiles, int colour, int phase, double inv_temp,
+                     unsigned long long seed, uint32_t sweep, bool acc, cudaStream_t s);
     void (*theta)(const BProb *probs, const int *map, int ntiles, int phase, int only_switched, double2 *partials,
                   cudaStream_t s);
     void (*reunit)(const BProb *probs, const int *map, int ntiles, int phase, bool acc, cudaStream_t s);
@@ -84,6 +87,15 @@ template <class P> struct BImpl {
             k_b_halfsweep<P, void><<<ntiles, kSweepTile, 0, s>>>(probs, map, colour, phase, omega, variant);
         count_launch();
     }
+    static void heatbath(const BProb *probs, const int *map, int ntiles, int colour, int phase, double inv_temp,
+                         unsigned long long seed, uint32_t sweep, bool acc, cudaStream_t s)
+    {
+        if (acc)
+            k_b_heatbath<P, PG><<<ntiles, kSweepTile, 0, s>>>(probs, map, colour, phase, inv_temp, seed, sweep);
+        else
+            k_b_heatbath<P, void><<<ntiles, kSweepTile, 0, s>>>(probs, map, colour, phase, inv_temp, seed, sweep);
+        count_launch();
+    }
     static void theta(const BProb *probs, const int *map, int ntiles, int phase, int only_switched,
                       double2 *partials, cudaStream_t s)
     {
@@ -126,6 +138,7 @@ template <class P> struct BImpl {
         BPhaseOps o;
         o.fp32 = kFP32;
         o.sweep = sweep;
+        o.heatbath = heatbath;
         o.theta = theta;
         o.reunit = reunit;
         o.temporal = temporal;

@@ -367,14 +367,29 @@ __device__ __forceinline__ void block_quaternion(const M3<T> &K, T &a0, T &a1, T
     a3 = K.im[I][I] - K.im[J][J];
 }
 
-// SU(3): subgroups (0,1), (0,2), (1,2) in that order, each maximising its
-// block of the running K (K <- R K) and overrelaxed; g = R12 R02 R01.
+// The SU(2) step of one subgroup in the local update of Sec. 2: the
+// overrelaxed maximiser. step(a0, a1, a2, a3, s, q) receives a quaternion
+// proportional to that of the block (twice it for the SU(3) blocks of
+// block_quaternion, the quaternion of K itself for SU(2)) and the subgroup
+// number s (0, 1, 2; 0 for SU(2)), and returns the unit quaternion q.
+template <typename T> struct OrStep {
+    T omega;
+    int variant;
+    __device__ __forceinline__ void operator()(T a0, T a1, T a2, T a3, int, T q[4]) const
+    {
+        su2_or_step(a0, a1, a2, a3, omega, variant, q);
+    }
+};
+
+// SU(3): subgroups (0,1), (0,2), (1,2) in that order, each updating its
+// block of the running K (K <- R K) by the given step; g = R12 R02 R01.
 // K is consumed.
-template <typename T> __device__ __forceinline__ void su3_local_gauge(M3<T> &K, M3<T> &g, T omega, int variant)
+template <typename T, class Step>
+__device__ __forceinline__ void su3_local_gauge_step(M3<T> &K, M3<T> &g, const Step &step)
 {
     T a0, a1, a2, a3, q[4];
     block_quaternion<T, 0, 1>(K, a0, a1, a2, a3);
-    su2_or_step(a0, a1, a2, a3, omega, variant, q);
+    step(a0, a1, a2, a3, 0, q);
     // g = R01
     g.re[0][0] = q[0];  g.im[0][0] = q[3];
     g.re[0][1] = q[2];  g.im[0][1] = q[1];
@@ -387,7 +402,7 @@ template <typename T> __device__ __forceinline__ void su3_local_gauge(M3<T> &K, 
     rotate_rows<T, 0, 1>(K, q);
 
     block_quaternion<T, 0, 2>(K, a0, a1, a2, a3);
-    su2_or_step(a0, a1, a2, a3, omega, variant, q);
+    step(a0, a1, a2, a3, 1, q);
     rotate_rows<T, 0, 2>(K, q);
     // g <- R02 g with g = R01 (row 2 = (0, 0, 1)): row 0 = n00 (g00, g01, 0) + n01 e2,
     // row 2 = n10 (g00, g01, 0) + n11 e2, n = [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]]
@@ -405,18 +420,28 @@ template <typename T> __device__ __forceinline__ void su3_local_gauge(M3<T> &K, 
     g.im[2][2] = -q[3];
 
     block_quaternion<T, 1, 2>(K, a0, a1, a2, a3);
-    su2_or_step(a0, a1, a2, a3, omega, variant, q);
+    step(a0, a1, a2, a3, 2, q);
     rotate_rows<T, 1, 2>(g, q);
+}
+
+template <typename T> __device__ __forceinline__ void su3_local_gauge(M3<T> &K, M3<T> &g, T omega, int variant)
+{
+    su3_local_gauge_step(K, g, OrStep<T>{omega, variant});
 }
 
 // SU(2): g = (K^+/sqrt(det K^+))^omega for the quaternion K = (k0, k):
 // the maximiser is (k0, -k)/|k|.
-template <typename T> __device__ __forceinline__ Q4<T> su2_local_gauge(const Q4<T> &K, T omega, int variant)
+template <typename T, class Step> __device__ __forceinline__ Q4<T> su2_local_gauge_step(const Q4<T> &K, const Step &step)
 {
     Q4<T> g;
-    // su2_or_step takes the quaternion of the block and conjugates it itself
-    su2_or_step(K.a[0], K.a[1], K.a[2], K.a[3], omega, variant, g.a);
+    // the step takes the quaternion of the block and conjugates it itself
+    step(K.a[0], K.a[1], K.a[2], K.a[3], 0, g.a);
     return g;
+}
+
+template <typename T> __device__ __forceinline__ Q4<T> su2_local_gauge(const Q4<T> &K, T omega, int variant)
+{
+    return su2_local_gauge_step(K, OrStep<T>{omega, variant});
 }
 
 // ---------------------------------------------------------------------------

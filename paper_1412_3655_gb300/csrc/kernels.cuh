@@ -56,10 +56,11 @@ __device__ __forceinline__ dfl shfl_pair(dfl v) { return dfl(shfl_pair(v.hi), sh
 // TPS = 2: this thread does the links of `half`; both lanes of a pair must
 // reach the shuffles, so an out-of-range pair passes valid = false instead
 // of returning.
-template <class P, bool KEEP, int TPS>
+// Step: the subgroup step of the local update (OrStep, or the heat bath of
+// the annealing kernels).
+template <class P, bool KEEP, int TPS, class Step>
 __device__ __forceinline__ void su3_update(typename P::Chunk *base, const Geom &g, int cb, int p, int half, bool valid,
-                                           int mu_first, typename P::Real omega, int variant,
-                                           M3<typename P::Real> *gout)
+                                           int mu_first, const Step &step, M3<typename P::Real> *gout)
 {
     typedef typename P::Real T;
     typedef typename P::Chunk C;
@@ -108,7 +109,7 @@ __device__ __forceinline__ void su3_update(typename P::Chunk *base, const Geom &
             }
     }
     M3<T> G;
-    su3_local_gauge(K, G, omega, variant);
+    su3_local_gauge_step(K, G, step);
 #pragma unroll
     for (int k = 0; k < NMU; k++) {
         const int mu = mu0 + k;
@@ -126,10 +127,9 @@ __device__ __forceinline__ void su3_update(typename P::Chunk *base, const Geom &
     if (gout) *gout = G;
 }
 
-template <class P, int TPS>
+template <class P, int TPS, class Step>
 __device__ __forceinline__ void su2_update(typename P::Chunk *base, const Geom &g, int cb, int p, int half, bool valid,
-                                           int mu_first, typename P::Real omega, int variant,
-                                           Q4<typename P::Real> *gout)
+                                           int mu_first, const Step &step, Q4<typename P::Real> *gout)
 {
     typedef typename P::Real T;
     typedef typename P::Chunk C;
@@ -167,7 +167,7 @@ __device__ __forceinline__ void su2_update(typename P::Chunk *base, const Geom &
             K.a[c] = half ? o + Ka.a[c] : Ka.a[c] + o;
         }
     }
-    Q4<T> G = su2_local_gauge(K, omega, variant);
+    Q4<T> G = su2_local_gauge_step(K, step);
 #pragma unroll
     for (int k = 0; k < NMU; k++) {
         const int mu = mu0 + k;
@@ -176,21 +176,6 @@ __device__ __forceinline__ void su2_update(typename P::Chunk *base, const Geom &
         P::store(bwd[k], g.stride, q_mul_adj(ub[k], G));
     }
     if (gout) *gout = G;
-}
-
-// one thread per site (the batched engine's mapping)
-template <class P, bool KEEP>
-__device__ __forceinline__ void su3_site_update(typename P::Chunk *base, const Geom &g, int cb, int p, int mu_first,
-                                                typename P::Real omega, int variant, M3<typename P::Real> *gout)
-{
-    su3_update<P, KEEP, 1>(base, g, cb, p, 0, true, mu_first, omega, variant, gout);
-}
-
-template <class P>
-__device__ __forceinline__ void su2_site_update(typename P::Chunk *base, const Geom &g, int cb, int p, int mu_first,
-                                                typename P::Real omega, int variant, Q4<typename P::Real> *gout)
-{
-    su2_update<P, 1>(base, g, cb, p, 0, true, mu_first, omega, variant, gout);
 }
 
 // links held between gather and update with two threads per site
@@ -203,6 +188,35 @@ template <class P> struct KeepLinks2 {
 // MINB are the launch bounds: MINB > 1 caps the registers at
 // 65536 / (MAXT MINB) so that MINB blocks fit on an SM (the autotuner's
 // register-limit axis).
+// gacc(x) <- g(x) gacc(x) for the site (cb, parity), when the accumulator
+// has the links' arithmetic type (the FP32 phase of the mixed schedule)
+template <class P, class PG>
+__device__ __forceinline__ void accumulate_gauge(typename PG::Chunk *gacc, const Geom &g, int parity, int cb,
+                                                 const M3<typename P::Real> &G)
+{
+    typedef typename P::Real T;
+    if constexpr (std::is_same<typename PG::Real, T>::value) {
+        typename PG::Chunk *gp = gacc + (size_t)parity * PG::NCHUNK * g.stride + cb;
+        M3<T> a, b;
+        PG::load(gp, g.stride, a);
+        m3_mul_rows<0, 1>(b, G, a);
+        PG::store(gp, g.stride, b);
+    }
+}
+
+template <class P, class PG>
+__device__ __forceinline__ void accumulate_gauge(typename PG::Chunk *gacc, const Geom &g, int parity, int cb,
+                                                 const Q4<typename P::Real> &G)
+{
+    typedef typename P::Real T;
+    if constexpr (std::is_same<typename PG::Real, T>::value) {
+        typename PG::Chunk *gp = gacc + (size_t)parity * PG::NCHUNK * g.stride + cb;
+        Q4<T> a;
+        PG::load(gp, g.stride, a);
+        PG::store(gp, g.stride, q_mul(G, a));
+    }
+}
+
 template <class P, int TPS, class PG, int MAXT = 256, int MINB = 1>
 __global__ void __launch_bounds__(MAXT, MINB) k_halfsweep_v(typename P::Chunk *base, typename PG::Chunk *gacc, Geom g,
                                                            int parity, typename P::Real omega, int variant, int acc)
@@ -212,30 +226,16 @@ __global__ void __launch_bounds__(MAXT, MINB) k_halfsweep_v(typename P::Chunk *b
     const int cb = t / TPS, half = t % TPS;
     const bool valid = cb < g.Vh;
     if (TPS == 1 && !valid) return;
+    const OrStep<T> step{omega, variant};
     if constexpr (P::NC == 3) {
         constexpr bool KEEP = TPS == 1 ? KeepLinks<P>::value : KeepLinks2<P>::value;
         M3<T> G;
-        su3_update<P, KEEP, TPS>(base, g, cb, parity, half, valid, 0, omega, variant, &G);
-        if constexpr (std::is_same<typename PG::Real, T>::value) {
-            if (acc && valid && half == 0) {
-                typename PG::Chunk *gp = gacc + (size_t)parity * PG::NCHUNK * g.stride + cb;
-                M3<T> a, b;
-                PG::load(gp, g.stride, a);
-                m3_mul_rows<0, 1>(b, G, a);
-                PG::store(gp, g.stride, b);
-            }
-        }
+        su3_update<P, KEEP, TPS>(base, g, cb, parity, half, valid, 0, step, &G);
+        if (acc && valid && half == 0) accumulate_gauge<P, PG>(gacc, g, parity, cb, G);
     } else {
         Q4<T> G;
-        su2_update<P, TPS>(base, g, cb, parity, half, valid, 0, omega, variant, &G);
-        if constexpr (std::is_same<typename PG::Real, T>::value) {
-            if (acc && valid && half == 0) {
-                typename PG::Chunk *gp = gacc + (size_t)parity * PG::NCHUNK * g.stride + cb;
-                Q4<T> a;
-                PG::load(gp, g.stride, a);
-                PG::store(gp, g.stride, q_mul(G, a));
-            }
-        }
+        su2_update<P, TPS>(base, g, cb, parity, half, valid, 0, step, &G);
+        if (acc && valid && half == 0) accumulate_gauge<P, PG>(gacc, g, parity, cb, G);
     }
 }
 
@@ -440,7 +440,6 @@ __global__ void __launch_bounds__(128) k_plaquette(const typename P::Chunk *base
 template <class P>
 __global__ void __launch_bounds__(256) k_reunitarize(typename P::Chunk *base, Geom g, int nplanes)
 {
-    typedef typename P::Real T;
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)nplanes * g.Vh) return;
     int plane = (int)(t / g.Vh);
@@ -448,13 +447,9 @@ __global__ void __launch_bounds__(256) k_reunitarize(typename P::Chunk *base, Ge
     typename P::Chunk *ptr = base + (size_t)plane * P::NCHUNK * g.stride + cb;
     typename P::Link u;
     P::load_raw(ptr, g.stride, u);
-    if constexpr (P::NC == 3) {
-        m3_reunitarize(u);
-    } else {
-        T n = T(1) / sqrt(u.a[0] * u.a[0] + u.a[1] * u.a[1] + u.a[2] * u.a[2] + u.a[3] * u.a[3]);
-#pragma unroll
-        for (int k = 0; k < 4; k++) u.a[k] *= n;
-    }
+    // the batched engine's reunitarisation uses the same function, so both
+    // paths round alike
+    reunitarize_link(u);
     P::store(ptr, g.stride, u);
 }
 

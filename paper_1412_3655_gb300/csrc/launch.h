@@ -33,6 +33,15 @@ struct Ops {
     // also accumulates g(x) per site. Every mapping gives the same result.
     void (*halfsweep)(void *base, void *gacc, const Geom &g, int parity, double omega, int variant, int tps,
                       int block, int minb, cudaStream_t s);
+    // one heat-bath half-sweep of the given parity at temperature 1/inv_temp
+    // (simulated annealing), draws keyed by (k0, k1) with sweep word `sweep`;
+    // one thread per site, blocks of 128; gacc as in halfsweep. variant picks
+    // one of heatbath_variants mappings (registers held / capped), all giving
+    // the same links.
+    void (*heatbath)(void *base, void *gacc, const Geom &g, int parity, double inv_temp, uint32_t k0, uint32_t k1,
+                     uint32_t sweep, int variant, cudaStream_t s);
+    int heatbath_variants;
+    void (*heatbath_mapping)(int variant, int *keep_links, int *min_blocks_per_sm);
     // per-block partial sums of (tr Delta Delta^+, sum Re tr U) over all sites; returns the block count
     int (*theta_partials)(const void *base, const Geom &g, int mu_first, double2 *partials, cudaStream_t s);
     // per-block partial sums of the plaquette trace; returns the block count

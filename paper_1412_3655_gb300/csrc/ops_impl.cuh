@@ -1,7 +1,7 @@
 // Launch wrappers for one storage parameterisation P; included by ops_*.cu.
 #pragma once
 
-#include "kernels.cuh"
+#include "anneal.cuh"
 #include "launch.h"
 
 namespace culgt {
@@ -42,6 +42,41 @@ template <class P> struct OpsImpl {
         else
             k_halfsweep_v<P, 1, PG><<<nb, block, 0, s>>>(b, a, g, parity, w, variant, acc);
         count_launch();
+    }
+    // variant: index into HbMappings<P> (out of range: 0)
+    static void heatbath(void *base, void *gacc, const Geom &g, int parity, double inv_temp, uint32_t k0, uint32_t k1,
+                         uint32_t sweep, int variant, cudaStream_t s)
+    {
+        typedef typename GaugeParam<P>::type PG;
+        typedef typename PG::Chunk GC;
+        const unsigned nb = blocks_for(g.Vh, 128);
+        const int acc = gacc != nullptr;
+        C *b = (C *)base;
+        GC *a = (GC *)gacc;
+        constexpr bool K0 = KeepLinks<P>::value;
+        if constexpr (HbMappings<P>::count == 5) {
+            switch (variant) {
+            case 1: k_heatbath<P, PG, true, 3><<<nb, 128, 0, s>>>(b, a, g, parity, inv_temp, k0, k1, sweep, acc); break;
+            case 2: k_heatbath<P, PG, false, 1><<<nb, 128, 0, s>>>(b, a, g, parity, inv_temp, k0, k1, sweep, acc); break;
+            case 3: k_heatbath<P, PG, false, 3><<<nb, 128, 0, s>>>(b, a, g, parity, inv_temp, k0, k1, sweep, acc); break;
+            case 4: k_heatbath<P, PG, false, 4><<<nb, 128, 0, s>>>(b, a, g, parity, inv_temp, k0, k1, sweep, acc); break;
+            default: k_heatbath<P, PG, true, 1><<<nb, 128, 0, s>>>(b, a, g, parity, inv_temp, k0, k1, sweep, acc);
+            }
+        } else if constexpr (HbMappings<P>::count == 2) {
+            if (variant == 1)
+                k_heatbath<P, PG, K0, 4><<<nb, 128, 0, s>>>(b, a, g, parity, inv_temp, k0, k1, sweep, acc);
+            else
+                k_heatbath<P, PG, K0, 1><<<nb, 128, 0, s>>>(b, a, g, parity, inv_temp, k0, k1, sweep, acc);
+        } else {
+            k_heatbath<P, PG, K0, 1><<<nb, 128, 0, s>>>(b, a, g, parity, inv_temp, k0, k1, sweep, acc);
+        }
+        count_launch();
+    }
+    static void heatbath_mapping(int variant, int *keep_links, int *min_blocks_per_sm)
+    {
+        const HbMapping m = HbMappings<P>::get(variant);
+        *keep_links = m.keep;
+        *min_blocks_per_sm = m.minb;
     }
     static int theta_partials(const void *base, const Geom &g, int mu_first, double2 *partials, cudaStream_t s)
     {
@@ -111,6 +146,9 @@ template <class P> struct OpsImpl {
         o.nchunk = P::NCHUNK;
         o.chunk_bytes = (int)sizeof(C);
         o.halfsweep = halfsweep;
+        o.heatbath = heatbath;
+        o.heatbath_variants = HbMappings<P>::count;
+        o.heatbath_mapping = heatbath_mapping;
         o.theta_partials = theta_partials;
         o.plaq_partials = plaq_partials;
         o.reunitarize = reunitarize;

@@ -66,6 +66,32 @@ class _Problem(ctypes.Structure):
     _fields_ = [("d_links", ctypes.c_void_p), ("dims", ctypes.c_int * 4)]
 
 
+class _AnnealParams(ctypes.Structure):
+    _fields_ = [
+        ("t_start", ctypes.c_double),
+        ("t_end", ctypes.c_double),
+        ("steps", ctypes.c_int),
+        ("micro_sweeps", ctypes.c_int),
+        ("seed", ctypes.c_ulonglong),
+    ]
+
+
+@dataclass
+class AnnealParams:
+    """Mirror of culgt_anneal_params (simulated annealing schedule)."""
+    t_start: float = 0.6
+    t_end: float = 0.01
+    steps: int = 500
+    micro_sweeps: int = 3
+    seed: int = 0
+
+    def _c(self) -> _AnnealParams:
+        a = _AnnealParams()
+        for name, _ in _AnnealParams._fields_:
+            setattr(a, name, getattr(self, name))
+        return a
+
+
 @dataclass
 class Params:
     """Mirror of culgt_params (see include/culgt.h for every field)."""
@@ -128,6 +154,7 @@ def library():
     lib = ctypes.CDLL(LIBRARY_PATH)
     vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
     P, R = ctypes.POINTER(_Params), ctypes.POINTER(_Result)
+    A = ctypes.POINTER(_AnnealParams)
     H = ctypes.c_void_p
     sigs = {
         "culgt_status_string": (ctypes.c_char_p, [ip]),
@@ -157,6 +184,13 @@ def library():
         "culgt_landau_fix_gauge": (ip, [vp, P, vp, R, vp]),
         "culgt_fix_batched": (ip, [ctypes.POINTER(_Problem), ip, P, vp, R]),
         "culgt_reunitarize": (ip, [vp, P, vp]),
+        "culgt_default_anneal_params": (ip, [A]),
+        "culgt_validate_anneal": (ip, [A]),
+        "culgt_handle_heatbath": (ip, [H, ctypes.c_double, ctypes.c_ulonglong, ctypes.c_uint]),
+        "culgt_handle_anneal": (ip, [H, A]),
+        "culgt_handle_heatbath_tuning": (ip, [H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+        "culgt_landau_fix_anneal": (ip, [vp, P, A, vp, R]),
+        "culgt_fix_batched_anneal": (ip, [ctypes.POINTER(_Problem), ip, P, A, vp, R]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -274,6 +308,49 @@ def culgt_coulomb_fix(links, params: Params, stream=None, gauge=None):
     return [Result._from(r, st) for r in rs]
 
 
+def _problems(links_list, dims_list, params: Params):
+    n = len(links_list)
+    if n != len(dims_list) or n == 0:
+        raise ValueError("need one dims entry per link tensor")
+    probs = (_Problem * n)()
+    for i, (t, dims) in enumerate(zip(links_list, dims_list)):
+        pi = Params(**{**params.__dict__, "dims": tuple(int(d) for d in dims)})
+        probs[i].d_links = _links_ptr(t, pi, True)
+        probs[i].dims = (ctypes.c_int * 4)(*[int(d) for d in dims])
+    return probs
+
+
+def culgt_default_anneal_params() -> AnnealParams:
+    a = _AnnealParams()
+    _check(library().culgt_default_anneal_params(ctypes.byref(a)), "culgt_default_anneal_params")
+    return AnnealParams(**{n: getattr(a, n) for n, _ in _AnnealParams._fields_})
+
+
+def culgt_validate_anneal(anneal: AnnealParams) -> int:
+    return int(library().culgt_validate_anneal(ctypes.byref(anneal._c())))
+
+
+def culgt_landau_fix_anneal(links, params: Params, anneal: AnnealParams, stream=None) -> Result:
+    """Simulated annealing (anneal's schedule), then Landau gauge fixing to
+    params.theta_target, in place."""
+    r = _Result()
+    st = _check(library().culgt_landau_fix_anneal(_links_ptr(links, params, True), ctypes.byref(params._c()),
+                                                  ctypes.byref(anneal._c()), _stream(stream), ctypes.byref(r)),
+                "culgt_landau_fix_anneal")
+    return Result._from(r, st)
+
+
+def culgt_fix_batched_anneal(links_list, dims_list, params: Params, anneal: AnnealParams, stream=None):
+    """culgt_fix_batched after annealing every problem (problem j draws with
+    seed + j). One Result per problem."""
+    probs = _problems(links_list, dims_list, params)
+    rs = (_Result * len(links_list))()
+    st = _check(library().culgt_fix_batched_anneal(probs, len(links_list), ctypes.byref(params._c()),
+                                                   ctypes.byref(anneal._c()), _stream(stream), rs),
+                "culgt_fix_batched_anneal")
+    return [Result._from(r, st) for r in rs]
+
+
 def culgt_fix_batched(links_list, dims_list, params: Params, stream=None):
     """Landau gauge fixing of several independent lattices (each a CUDA tensor
     in the canonical layout, dims from dims_list) in shared launches; nc,
@@ -385,6 +462,20 @@ class Handle:
         _check(library().culgt_handle_tuning(self._h, ctypes.byref(t), ctypes.byref(b), ctypes.byref(m)),
                "culgt_handle_tuning")
         return t.value, b.value, m.value
+
+    def culgt_handle_heatbath(self, T: float, seed: int, sweep_word: int):
+        _check(library().culgt_handle_heatbath(self._h, float(T), int(seed), int(sweep_word)),
+               "culgt_handle_heatbath")
+
+    def culgt_handle_heatbath_tuning(self):
+        """(keep links in registers, min blocks per SM) of the heat-bath sweeps."""
+        k, m = ctypes.c_int(), ctypes.c_int()
+        _check(library().culgt_handle_heatbath_tuning(self._h, ctypes.byref(k), ctypes.byref(m)),
+               "culgt_handle_heatbath_tuning")
+        return k.value, m.value
+
+    def culgt_handle_anneal(self, anneal: AnnealParams):
+        _check(library().culgt_handle_anneal(self._h, ctypes.byref(anneal._c())), "culgt_handle_anneal")
 
     def culgt_handle_fix(self) -> Result:
         r = _Result()

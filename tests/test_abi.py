@@ -106,3 +106,40 @@ def test_workspace_bytes(lib):
     b2 = lib.culgt_workspace_bytes(p)
     # mixed: FP32 12-real and FP64 18-real links plus the FP32 gauge accumulator
     assert b2 == pytest.approx(4 * V * (144 + 48) + V * 48, rel=0.01)
+
+
+def test_anneal_defaults_validate(lib):
+    a = lib.culgt_default_anneal_params()
+    assert (a.t_start, a.t_end, a.steps, a.micro_sweeps, a.seed) == (0.6, 0.01, 500, 3, 0)
+    assert lib.culgt_validate_anneal(a) == lib.OK
+    assert lib.culgt_validate_anneal(lib.AnnealParams(seed=2 ** 64 - 1, steps=0)) == lib.OK
+
+
+@pytest.mark.parametrize("change", [
+    {"t_start": 0.0}, {"t_end": -1.0}, {"t_start": float("inf")}, {"t_end": float("nan")},
+    {"steps": -1}, {"micro_sweeps": -2},
+])
+def test_anneal_validate_rejects(lib, change):
+    a = lib.AnnealParams(**change)
+    assert lib.culgt_validate_anneal(a) == lib.ERR_ARG
+    # the annealing entry points check before touching the device
+    so = lib.library()
+    p = lib.Params.defaults(3, (4, 4, 4, 4))
+    assert so.culgt_landau_fix_anneal(ctypes.c_void_p(16), ctypes.byref(p._c()), ctypes.byref(a._c()), None,
+                                      None) == lib.ERR_ARG
+    probs = (lib._Problem * 1)()
+    probs[0].d_links = 16
+    probs[0].dims = (ctypes.c_int * 4)(4, 4, 4, 4)
+    assert so.culgt_fix_batched_anneal(probs, 1, ctypes.byref(p._c()), ctypes.byref(a._c()), None,
+                                       None) == lib.ERR_ARG
+
+
+def test_anneal_null_arguments_rejected(lib):
+    so = lib.library()
+    p = lib.Params.defaults(3, (4, 4, 4, 4))
+    a = lib.AnnealParams()
+    assert so.culgt_landau_fix_anneal(ctypes.c_void_p(16), ctypes.byref(p._c()), None, None, None) == lib.ERR_ARG
+    assert so.culgt_landau_fix_anneal(None, ctypes.byref(p._c()), ctypes.byref(a._c()), None, None) == lib.ERR_ARG
+    assert so.culgt_handle_anneal(None, ctypes.byref(a._c())) == lib.ERR_ARG
+    assert so.culgt_handle_heatbath(None, 1.0, 0, 0) == lib.ERR_ARG
+    assert so.culgt_default_anneal_params(None) == lib.ERR_ARG

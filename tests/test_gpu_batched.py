@@ -121,12 +121,13 @@ def test_batched_uneven_lattices(cu, orc, nc, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
-def test_batched_single_problem_matches_handle(cu, precision):
+@pytest.mark.parametrize("nc", [2, 3])
+def test_batched_single_problem_matches_handle(cu, nc, precision):
     prec = {"fp64": 0, "fp32": 1, "mixed": 2}[precision]
     dims = (4, 4, 4, 4)
-    U = synth.gauge_config(dims, 3, 0.3, 1)
+    U = synth.gauge_config(dims, nc, 0.3, 1)
     target = 1e-10 if prec == 1 else 1e-12
-    p = cu.Params.defaults(3, dims, precision=prec, check_every=5, reunit_every=50, theta_target=target)
+    p = cu.Params.defaults(nc, dims, precision=prec, check_every=5, reunit_every=50, theta_target=target)
     a = to_dev(U)
     ra = cu.culgt_landau_fix(a, p)
     b = to_dev(U)
