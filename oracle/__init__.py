@@ -4,7 +4,7 @@ A thin ctypes binding over ``culgt_oracle.c``: a plain, slow restatement of
 lattice Landau/Coulomb gauge fixing as defined in Vogt & Schröck, "cuLGT:
 Lattice Gauge Fixing on GPUs", Sec. 2, and of the simulated annealing the paper
 combines with it (heat bath over the SU(2) subgroups, readings R7-R11 in
-``culgt_oracle.c``). Only the tests, ``__graft_entry__.smoke``
+``culgt_oracle.c``), and of maximally Abelian gauge fixing (R12-R15). Only the tests, ``__graft_entry__.smoke``
 and the CPU-baseline leg of ``bench.py`` use this module; the CUDA library never
 does, and the two share no code.
 
@@ -69,6 +69,12 @@ def _load():
         "oracle_heatbath_sweep": (None, [dp, ip, i, d, u32p, ctypes.c_uint32, dp]),
         "oracle_micro_sweep": (None, [dp, ip, i]),
         "oracle_anneal": (None, [dp, ip, i, d, d, i, i, u32p, i]),
+        "oracle_mag_halfsweep": (None, [dp, ip, i, i, d, i]),
+        "oracle_mag_sweep": (None, [dp, ip, i, d, i, i]),
+        "oracle_mag_theta": (None, [dp, ip, i, dp, dp]),
+        "oracle_mag_fix": (i, [dp, ip, i, d, i, d, i, i, i, ip, dp, dp]),
+        "oracle_mag_local_gauge": (None, [dp, i, d, i, dp]),
+        "oracle_mag_su2_max": (None, [dp, dp]),
         "oracle_set_threads": (None, [i]),
         "oracle_get_threads": (i, []),
     }
@@ -268,3 +274,49 @@ def anneal(U, L, nc, t_start, t_end, steps, n_micro, seed, reunit_every=0):
     _check_links(U, L, nc)
     _load().oracle_anneal(_dp(U), _dims(L), nc, float(t_start), float(t_end), int(steps), int(n_micro),
                           _key(seed), int(reunit_every))
+
+
+# --- maximally Abelian gauge (readings R12-R15 of culgt_oracle.c) ---
+
+def mag_halfsweep(U, L, nc, parity, omega, variant=0):
+    _check_links(U, L, nc)
+    _load().oracle_mag_halfsweep(_dp(U), _dims(L), nc, int(parity), float(omega), int(variant))
+
+
+def mag_sweep(U, L, nc, omega, n_sweeps=1, variant=0):
+    _check_links(U, L, nc)
+    _load().oracle_mag_sweep(_dp(U), _dims(L), nc, float(omega), int(variant), int(n_sweeps))
+
+
+def mag_theta(U, L, nc):
+    """(theta_MAG, F_MAG)."""
+    _check_links(U, L, nc)
+    th, F = ctypes.c_double(), ctypes.c_double()
+    _load().oracle_mag_theta(_dp(U), _dims(L), nc, ctypes.byref(th), ctypes.byref(F))
+    return th.value, F.value
+
+
+def mag_fix(U, L, nc, omega, theta_target, max_sweeps, check_every=1, reunit_every=0, variant=0):
+    """MAG fixing in place. Returns dict(converged, sweeps, theta, F)."""
+    _check_links(U, L, nc)
+    n, th, F = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    rc = _load().oracle_mag_fix(_dp(U), _dims(L), nc, float(omega), int(variant), float(theta_target),
+                                int(max_sweeps), int(check_every), int(reunit_every), ctypes.byref(n),
+                                ctypes.byref(th), ctypes.byref(F))
+    return {"converged": rc == 0, "sweeps": n.value, "theta": th.value, "F": F.value}
+
+
+def mag_local_gauge(X, omega, variant=0):
+    """The MAG site transformation for X_0..X_{Nc-1} (array (Nc, Nc, Nc)); returns (g, rotated X)."""
+    X = np.ascontiguousarray(X, dtype=np.complex128).copy()
+    nc = X.shape[-1]
+    g = np.zeros((nc, nc), dtype=np.complex128)
+    _load().oracle_mag_local_gauge(_dp(X), nc, float(omega), int(variant), _dp(g))
+    return g, X
+
+
+def mag_su2_max(Z):
+    Z = np.ascontiguousarray(Z, dtype=np.complex128)
+    B = np.zeros((2, 2), dtype=np.complex128)
+    _load().oracle_mag_su2_max(_dp(Z), _dp(B))
+    return B

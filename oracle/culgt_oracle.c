@@ -48,6 +48,13 @@
  *   R11 Schedule: T linear from t_start to t_end over `steps` heat-bath
  *       sweeps, each followed by n_micro microcanonical sweeps (omega = 2);
  *       reunitarisation counts sweeps of both kinds.
+ *   R12 Maximally Abelian gauge (named, not specified, by the paper): the
+ *       functional is sum_{x,mu} sum_a |U_mu(x)_aa|^2, normalised by Nd Nc V.
+ *   R13 Its SU(2) (subgroup) maximiser is the smallest rotation taking the
+ *       vector z of the block of X_i - X_j to +|z| e3.
+ *   R14 SU(3): the subgroups of R1, running X_a rotated by every step, each
+ *       step overrelaxed as in R3.
+ *   R15 theta_MAG = (1/V) sum_x sum_{i != j} |(X_i - X_j)_ij|^2.
  */
 #include <math.h>
 #include <stddef.h>
@@ -938,6 +945,209 @@ void oracle_anneal(double *U, const int *L, int nc, double t_start, double t_end
             if (reunit_every > 0 && done % reunit_every == 0) oracle_reunitarize(U, lat.V * 4, nc);
         }
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* maximally Abelian gauge (abstract, Sec. 1; readings R12-R15)        */
+/* ------------------------------------------------------------------ */
+
+/* R12: the MAG functional is F_MAG = 1/(Nd Nc V) sum_{x,mu} sum_a |U_mu(x)_aa|^2
+ * (1 when every link is diagonal). With the diagonal projectors P_a, the
+ * part of it that depends on g(x) is sum_a tr[P_a g X_a g^+] with
+ *   X_a(x) = sum_mu [U_mu(x) P_a U_mu(x)^+ + U_mu(x-mu)^+ P_a U_mu(x-mu)],
+ * since |(g U)_aa|^2 = tr[P_a g U P_a U^+ g^+] and
+ * |(U g^+)_aa|^2 = tr[P_a g U^+ P_a U g^+]. */
+static void mag_X(const double *U, const lattice *lat, int nc, long i, mat *X)
+{
+    for (int a = 0; a < nc; a++) X[a] = mat_zero(nc);
+    for (int mu = 0; mu < 4; mu++) {
+        mat f = get_link(U, nc, i, mu);
+        mat b = get_link(U, nc, site_shift(lat, i, mu, -1), mu);
+        mat fd = mat_adj(&f), bd = mat_adj(&b);
+        for (int a = 0; a < nc; a++) {
+            mat Pa = mat_zero(nc);
+            Pa.m[a][a] = c_make(1.0, 0.0);
+            mat t = mat_mul(&f, &Pa);
+            t = mat_mul(&t, &fd);
+            X[a] = mat_add(&X[a], &t);
+            t = mat_mul(&bd, &Pa);
+            t = mat_mul(&t, &b);
+            X[a] = mat_add(&X[a], &t);
+        }
+    }
+}
+
+/* R13: for an SU(2) element B acting on rows and columns (i, j), the
+ * g-dependent part of the local functional is (1/2) tr[s3 B Z B^+] + const
+ * with Z the (i, j) block of X_i - X_j. Writing the traceless part of Z as
+ * z.s, this is (R(B) z)_3, R(B) the rotation B induces; its maximum |z| is
+ * reached by the smallest rotation taking z to +|z| e3,
+ *   B = (|z| 1 + s3 (z.s)) / sqrt(2 |z| (|z| + z3)).
+ * z = 0 leaves the block alone; z = -|z| e3 takes B = i s1. */
+static mat mag_su2_max(const mat *Z)
+{
+    double z3 = 0.5 * (Z->m[0][0].re - Z->m[1][1].re);
+    double z1 = Z->m[0][1].re, z2 = -Z->m[0][1].im; /* Z_01 = z1 - i z2 */
+    double n = sqrt(z1 * z1 + z2 * z2 + z3 * z3);
+    mat B = mat_zero(2);
+    if (!(n > 0.0)) return mat_identity(2);
+    if (n + z3 == 0.0) {
+        B.m[0][1] = c_make(0.0, 1.0);
+        B.m[1][0] = c_make(0.0, 1.0);
+        return B;
+    }
+    /* s3 (z.s) = [[z3, z1 - i z2], [-(z1 + i z2), z3]] */
+    B.m[0][0] = c_make(n + z3, 0.0);
+    B.m[0][1] = c_make(z1, -z2);
+    B.m[1][0] = c_make(-z1, -z2);
+    B.m[1][1] = c_make(n + z3, 0.0);
+    cplx s = c_sqrt(mat_det2(&B));
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++) B.m[a][b] = c_div(B.m[a][b], s);
+    return B;
+}
+
+/* R14: the MAG site transformation: SU(2) directly, SU(3) over the subgroups
+ * of R1, each maximising its block and overrelaxed (R3), the running X_a
+ * rotated by every subgroup update (X_a <- R X_a R^+, g <- R g). */
+static mat mag_local_gauge(mat *X, int nc, double omega, int variant)
+{
+    static const int sub[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    int nsub = nc == 2 ? 1 : 3;
+    mat g = mat_identity(nc);
+    for (int s = 0; s < nsub; s++) {
+        int i = sub[s][0], j = sub[s][1];
+        mat D = mat_sub(&X[i], &X[j]);
+        mat Z = mat_zero(2);
+        Z.m[0][0] = D.m[i][i];
+        Z.m[0][1] = D.m[i][j];
+        Z.m[1][0] = D.m[j][i];
+        Z.m[1][1] = D.m[j][j];
+        mat r = mag_su2_max(&Z);
+        r = overrelax(&r, omega, variant);
+        mat R = mat_identity(nc);
+        R.m[i][i] = r.m[0][0];
+        R.m[i][j] = r.m[0][1];
+        R.m[j][i] = r.m[1][0];
+        R.m[j][j] = r.m[1][1];
+        mat Rd = mat_adj(&R);
+        for (int a = 0; a < nc; a++) {
+            mat t = mat_mul(&R, &X[a]);
+            X[a] = mat_mul(&t, &Rd);
+        }
+        g = mat_mul(&R, &g);
+    }
+    return g;
+}
+
+static void mag_update_site(double *U, const lattice *lat, int nc, long i, double omega, int variant)
+{
+    mat X[3];
+    mag_X(U, lat, nc, i, X);
+    mat g = mag_local_gauge(X, nc, omega, variant);
+    mat gd = mat_adj(&g);
+    for (int mu = 0; mu < 4; mu++) {
+        long ib = site_shift(lat, i, mu, -1);
+        mat f = get_link(U, nc, i, mu);
+        mat b = get_link(U, nc, ib, mu);
+        mat fn = mat_mul(&g, &f);
+        mat bn = mat_mul(&b, &gd);
+        put_link(U, nc, i, mu, &fn);
+        put_link(U, nc, ib, mu, &bn);
+    }
+}
+
+void oracle_mag_halfsweep(double *U, const int *L, int nc, int parity, double omega, int variant)
+{
+    lattice lat = make_lattice(L);
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < lat.V; i++)
+        if (site_parity(&lat, i, 0) == parity) mag_update_site(U, &lat, nc, i, omega, variant);
+}
+
+void oracle_mag_sweep(double *U, const int *L, int nc, double omega, int variant, int n_sweeps)
+{
+    for (int s = 0; s < n_sweeps; s++) {
+        oracle_mag_halfsweep(U, L, nc, 0, omega, variant);
+        oracle_mag_halfsweep(U, L, nc, 1, omega, variant);
+    }
+}
+
+/* R15: the MAG condition is the stationarity of the local functional at
+ * g = 1: its gradient sum_a [X_a, P_a] has the entries (X_j - X_i)_ij off the
+ * diagonal (and 0 on it). theta_MAG = (1/V) sum_x sum_{i != j} |(X_i - X_j)_ij|^2;
+ * F_MAG as in R12. Per-site values are summed in site order. */
+void oracle_mag_theta(const double *U, const int *L, int nc, double *theta, double *F)
+{
+    lattice lat = make_lattice(L);
+    double *th = (double *)malloc(sizeof(double) * lat.V);
+    double *ff = (double *)malloc(sizeof(double) * lat.V);
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < lat.V; i++) {
+        mat X[3];
+        mag_X(U, &lat, nc, i, X);
+        double t = 0.0;
+        for (int a = 0; a < nc; a++)
+            for (int b = 0; b < nc; b++)
+                if (a != b) t += c_abs2(c_sub(X[a].m[a][b], X[b].m[a][b]));
+        th[i] = t;
+        double f = 0.0;
+        for (int mu = 0; mu < 4; mu++) {
+            mat u = get_link(U, nc, i, mu);
+            for (int a = 0; a < nc; a++) f += c_abs2(u.m[a][a]);
+        }
+        ff[i] = f;
+    }
+    double st = 0.0, sf = 0.0;
+    for (long i = 0; i < lat.V; i++) {
+        st += th[i];
+        sf += ff[i];
+    }
+    free(th);
+    free(ff);
+    *theta = st / (double)lat.V;
+    *F = sf / (4.0 * nc * (double)lat.V);
+}
+
+/* MAG fixing, with the stopping and reunitarisation rules of oracle_landau_fix. */
+int oracle_mag_fix(double *U, const int *L, int nc, double omega, int variant, double theta_target, int max_sweeps,
+                   int check_every, int reunit_every, int *sweeps_out, double *theta_out, double *F_out)
+{
+    lattice lat = make_lattice(L);
+    double th, F;
+    int n = 0;
+    oracle_mag_theta(U, L, nc, &th, &F);
+    while (!(th < theta_target) && n < max_sweeps) {
+        for (int k = 0; k < check_every && n < max_sweeps; k++) {
+            oracle_mag_sweep(U, L, nc, omega, variant, 1);
+            n++;
+            if (reunit_every > 0 && n % reunit_every == 0) oracle_reunitarize(U, lat.V * 4, nc);
+        }
+        oracle_mag_theta(U, L, nc, &th, &F);
+    }
+    *sweeps_out = n;
+    *theta_out = th;
+    *F_out = F;
+    return th < theta_target ? 0 : 1;
+}
+
+/* the MAG site transformation for given X_0 .. X_{Nc-1} (Nc x Nc each); X is
+ * rotated in place as the subgroup steps go */
+void oracle_mag_local_gauge(double *X, int nc, double omega, int variant, double *g)
+{
+    mat Xm[3];
+    for (int a = 0; a < nc; a++) Xm[a] = get_mat(X, nc, a);
+    mat r = mag_local_gauge(Xm, nc, omega, variant);
+    for (int a = 0; a < nc; a++) put_mat(X, nc, a, &Xm[a]);
+    put_mat(g, nc, 0, &r);
+}
+
+/* the SU(2) maximiser of (1/2) tr[s3 B Z B^+] for a 2x2 hermitian Z */
+void oracle_mag_su2_max(const double *Z, double *B)
+{
+    mat z = get_mat(Z, 2, 0);
+    mat b = mag_su2_max(&z);
+    put_mat(B, 2, 0, &b);
 }
 
 /* ------------------------------------------------------------------ */
