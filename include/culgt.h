@@ -66,6 +66,20 @@ typedef enum {
  *   CULGT_DF        double-float sweeps throughout. */
 typedef enum { CULGT_FP64 = 0, CULGT_FP32 = 1, CULGT_MIXED = 2, CULGT_MIXED_DF = 3, CULGT_DF = 4 } culgt_precision;
 
+/* The gauge functional (culgt_params.gauge).
+ *   CULGT_LANDAU  F = 1/(4 Nc V) sum_{x,mu} Re tr U_mu(x) (Sec. 2); theta as
+ *                 in the Landau entries below. Coulomb gauge is the same
+ *                 functional per time slice (culgt_coulomb_fix).
+ *   CULGT_MAG     maximally Abelian gauge, named by the paper (abstract) without
+ *                 formulas; our reading: F_MAG = 1/(4 Nc V) sum_{x,mu} sum_a
+ *                 |U_mu(x)_aa|^2, maximised site by site over the SU(2)
+ *                 subgroups with the same checkerboard overrelaxation, and
+ *                 theta_MAG = (1/V) sum_x sum_{i != j} |(X_i - X_j)_ij|^2 with
+ *                 X_a(x) = sum_mu [U_mu(x) P_a U_mu(x)^+ + U_mu(x-mu)^+ P_a U_mu(x-mu)],
+ *                 P_a the diagonal projectors (theta_MAG = 0 at a stationary
+ *                 point of the functional). */
+typedef enum { CULGT_LANDAU = 0, CULGT_MAG = 1 } culgt_gauge;
+
 typedef struct {
     int dims[4];         /* L0 (time), L1, L2, L3; all even, >= 2 */
     int nc;              /* 2 = SU(2), 3 = SU(3) */
@@ -85,6 +99,7 @@ typedef struct {
     int block_size;       /* half-sweep threads per block: 64, 128 or 256; 0 = autotune */
     int min_blocks_per_sm; /* register limit: 1 = none, 3 or 4 blocks of 128 per SM (at most 168 / 128
                               registers, block_size 128); 0 = autotune */
+    int gauge;            /* culgt_gauge: the functional the handle API maximises (0 = Landau) */
 } culgt_params;
 
 typedef struct {
@@ -124,7 +139,8 @@ culgt_status culgt_workspace_bytes(const culgt_params *p, size_t *bytes);
  * A handle owns the links in the internal checkerboard structure-of-arrays
  * layout (Sec. 3.1: parities split, site index fastest), plus reduction
  * scratch. It is bound to one stream and must not be used from two host
- * threads at once. */
+ * threads at once. Its sweeps, theta and fix use the functional p->gauge
+ * names (Landau or MAG). */
 
 culgt_status culgt_create(const culgt_params *p, void *cuda_stream, culgt_handle **out);
 void culgt_destroy(culgt_handle *h);
@@ -149,7 +165,8 @@ culgt_status culgt_handle_to_fp64(culgt_handle *h);
 /* The half-sweep mapping the handle uses. Unless the parameters fix a single
  * mapping, the first sweep times every allowed one (threads per site, block
  * size, register limit; Sec. 5's autotuner) on a scratch copy of the links
- * and keeps the fastest for this storage and volume in the process. Lattices
+ * and keeps, for this storage and volume in the process, the first in its
+ * list within 2% of the fastest. Lattices
  * below 65536 sites take the first allowed mapping untimed. The mappings give
  * bitwise identical links; only their speed differs. */
 culgt_status culgt_handle_tuning(culgt_handle *h, int *threads_per_site, int *block_size, int *min_blocks_per_sm);
@@ -160,12 +177,20 @@ culgt_status culgt_handle_fix(culgt_handle *h, culgt_result *out);
 /* ---- one-call API (allocates and frees a handle inside) ---------------- */
 
 /* Landau gauge fixing of d_links in place. out may be NULL. Returns
- * CULGT_NOT_CONVERGED (with the links still written back) if max_sweeps ran out. */
+ * CULGT_NOT_CONVERGED (with the links still written back) if max_sweeps ran
+ * out. This and the other Landau/Coulomb one-call, batched and annealing
+ * entry points need p->gauge = CULGT_LANDAU (else CULGT_ERR_ARG). */
 culgt_status culgt_landau_fix(void *d_links, const culgt_params *p, void *cuda_stream, culgt_result *out);
 
 /* Same, on a HOST buffer (pageable or pinned): host -> device copy, fix,
  * device -> host copy, all inside the call. */
 culgt_status culgt_landau_fix_host(void *h_links, const culgt_params *p, void *cuda_stream, culgt_result *out);
+
+/* Maximally Abelian gauge fixing of d_links in place (CULGT_MAG, whatever
+ * p->gauge says): sweeps to theta_MAG < theta_target at the given precision,
+ * with the mixed schedule and its orbit-exact switch as for Landau gauge.
+ * out->theta and out->F are theta_MAG and F_MAG. */
+culgt_status culgt_mag_fix(void *d_links, const culgt_params *p, void *cuda_stream, culgt_result *out);
 
 /* Coulomb gauge fixing in place: one 3D problem per time slice over mu =
  * 1..3, each stopping at its own theta_t < theta_target; the accumulated
@@ -184,10 +209,11 @@ culgt_status culgt_coulomb_fix(void *d_links, const culgt_params *p, void *cuda_
 culgt_status culgt_landau_fix_gauge(void *d_links, const culgt_params *p, void *cuda_stream, culgt_result *out,
                                     void *d_gauge);
 
-/* n_sweeps sweeps of d_links in place at the given precision. */
+/* n_sweeps sweeps of d_links in place at the given precision, for the
+ * functional p->gauge names. */
 culgt_status culgt_sweep(void *d_links, const culgt_params *p, int n_sweeps, void *cuda_stream);
 
-/* theta and F of d_links (either pointer may be NULL). */
+/* theta and F of d_links for the functional p->gauge names (either pointer may be NULL). */
 culgt_status culgt_theta(const void *d_links, const culgt_params *p, void *cuda_stream, double *theta, double *F);
 
 /* theta and F like culgt_theta, for callers that cannot allocate device

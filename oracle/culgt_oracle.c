@@ -991,7 +991,7 @@ static mat mag_su2_max(const mat *Z)
     double n = sqrt(z1 * z1 + z2 * z2 + z3 * z3);
     mat B = mat_zero(2);
     if (!(n > 0.0)) return mat_identity(2);
-    if (n + z3 == 0.0) {
+    if (!(n + z3 > 0.0)) { /* z on (or by rounding past) -e3 */
         B.m[0][1] = c_make(0.0, 1.0);
         B.m[1][0] = c_make(0.0, 1.0);
         return B;

@@ -110,7 +110,16 @@ culgt_status validate(const culgt_params *p)
     if (p->min_blocks_per_sm != 0 && p->min_blocks_per_sm != 1 && p->min_blocks_per_sm != 3 &&
         p->min_blocks_per_sm != 4)
         return CULGT_ERR_ARG;
+    if (p->gauge != CULGT_LANDAU && p->gauge != CULGT_MAG) return CULGT_ERR_ARG;
     return CULGT_OK;
+}
+
+// the Landau-only entry points (one-call Landau, Coulomb, batched, annealing)
+culgt_status validate_landau(const culgt_params *p)
+{
+    culgt_status st = validate(p);
+    if (st != CULGT_OK) return st;
+    return p->gauge == CULGT_LANDAU ? CULGT_OK : CULGT_ERR_ARG;
 }
 
 size_t buffer_bytes(const Ops *o, const Geom &g) { return (size_t)8 * o->nchunk * g.stride * o->chunk_bytes; }
@@ -159,7 +168,8 @@ culgt_status sync_scalars(culgt_handle *h, int n)
 void theta_enqueue(culgt_handle *h)
 {
     const Geom &g = h->geom;
-    int nb = cur_ops(h)->theta_partials(cur_buf(h), g, 0, h->partials, h->stream);
+    int nb = h->prm.gauge == CULGT_MAG ? cur_ops(h)->mag_theta_partials(cur_buf(h), g, h->partials, h->stream)
+                                       : cur_ops(h)->theta_partials(cur_buf(h), g, 0, h->partials, h->stream);
     launch_finalize2(h->partials, nb, 1.0 / g.V, 1.0 / (4.0 * h->prm.nc * g.V), h->d_scalars, h->stream);
     cudaMemcpyAsync(h->h_scalars, h->d_scalars, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
 }
@@ -201,10 +211,12 @@ culgt_status unitarity_now(culgt_handle *h, double *err)
 
 // Autotuner (the paper's runtime choice of kernel settings, Sec. 5): each
 // (threads per site, block size) mapping is timed on a scratch copy of the
-// links; the fastest is kept per (storage, lattice volume, accumulation) for
-// the process. All mappings give bitwise identical links, so the choice never
-// changes a result. Lattices below kTuneMinSites use the default mapping.
+// links; the first one in list order within 2% of the fastest is kept per
+// (storage, lattice volume, accumulation) for the process. All mappings give
+// bitwise identical links, so the choice never changes a result. Lattices
+// below kTuneMinSites use the default mapping.
 constexpr int kTuneMinSites = 1 << 16;
+constexpr float kTuneSlack = 1.02f;
 std::mutex g_tune_mutex;
 
 struct Mapping {
@@ -263,26 +275,34 @@ culgt_status autotune(culgt_handle *h, const Ops *o, void *buf, bool acc, Mappin
     cudaEventCreate(&e1);
     CU(cudaMemcpyAsync(scratch, buf, bytes, cudaMemcpyDeviceToDevice, h->stream));
     if (acc) CU(cudaMemcpyAsync(gscratch, h->gacc, gbytes, cudaMemcpyDeviceToDevice, h->stream));
+    float times[sizeof(kMappings) / sizeof(kMappings[0])];
     float best = 1e30f;
-    Mapping pick = only;
+    int idx = 0;
     for (const Mapping &m : kMappings) {
-        if (!mapping_allowed(p, m)) continue;
-        o->halfsweep(scratch, gscratch, h->geom, 0, p.omega, p.or_variant, m.tps, m.block, m.minb, h->stream);
-        cudaEventRecord(e0, h->stream);
-        for (int r = 0; r < 2; r++)
-            for (int parity = 0; parity < 2; parity++)
-                o->halfsweep(scratch, gscratch, h->geom, parity, p.omega, p.or_variant, m.tps, m.block, m.minb,
-                             h->stream);
-        cudaEventRecord(e1, h->stream);
-        cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        count_launch(-5);  // tuning launches are not part of the caller's work
-        if (ms < best) {
-            best = ms;
-            pick = m;
+        times[idx] = 1e30f;
+        if (mapping_allowed(p, m)) {
+            o->halfsweep(scratch, gscratch, h->geom, 0, p.omega, p.or_variant, m.tps, m.block, m.minb, h->stream);
+            cudaEventRecord(e0, h->stream);
+            for (int r = 0; r < 2; r++)
+                for (int parity = 0; parity < 2; parity++)
+                    o->halfsweep(scratch, gscratch, h->geom, parity, p.omega, p.or_variant, m.tps, m.block, m.minb,
+                                 h->stream);
+            cudaEventRecord(e1, h->stream);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&times[idx], e0, e1);
+            count_launch(-5);  // tuning launches are not part of the caller's work
+            if (times[idx] < best) best = times[idx];
         }
+        idx++;
     }
+    // the first mapping (list order) within kTuneSlack of the fastest: timing
+    // noise between near-equal mappings does not flip the choice
+    Mapping pick = only;
+    for (int k = 0; k < idx; k++)
+        if (times[k] <= best * kTuneSlack) {
+            pick = kMappings[k];
+            break;
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(scratch);
@@ -315,11 +335,17 @@ culgt_status tuned_mapping(culgt_handle *h, Mapping *m)
 // In the FP32 phase of a mixed handle the half-sweeps also accumulate g(x).
 culgt_status sweep_now(culgt_handle *h, int n)
 {
-    Mapping m;
-    ST(tuned_mapping(h, &m));
     const Ops *o = cur_ops(h);
     void *b = cur_buf(h);
     void *acc = (h->cur32 && h->gacc) ? h->gacc : nullptr;
+    if (h->prm.gauge == CULGT_MAG) {
+        for (int k = 0; k < n; k++)
+            for (int parity = 0; parity < 2; parity++)
+                o->mag_halfsweep(b, acc, h->geom, parity, h->prm.omega, h->prm.or_variant, h->stream);
+        return CULGT_OK;
+    }
+    Mapping m;
+    ST(tuned_mapping(h, &m));
     for (int k = 0; k < n; k++)
         for (int parity = 0; parity < 2; parity++)
             o->halfsweep(b, acc, h->geom, parity, h->prm.omega, h->prm.or_variant, m.tps, m.block, m.minb, h->stream);
@@ -389,8 +415,9 @@ culgt_status tuned_heatbath(culgt_handle *h, int *variant)
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
-            float best = 1e30f;
-            for (int v = 0; v < o->heatbath_variants; v++) {
+            float best = 1e30f, times[8];
+            const int nv = o->heatbath_variants < 8 ? o->heatbath_variants : 8;
+            for (int v = 0; v < nv; v++) {
                 o->heatbath(scratch, gscratch, h->geom, 0, 1.0, 0u, 0u, 0u, v, h->stream);
                 cudaEventRecord(e0, h->stream);
                 for (int r = 0; r < 2; r++)
@@ -398,14 +425,16 @@ culgt_status tuned_heatbath(culgt_handle *h, int *variant)
                         o->heatbath(scratch, gscratch, h->geom, parity, 1.0, 0u, 0u, (unsigned)r, v, h->stream);
                 cudaEventRecord(e1, h->stream);
                 cudaEventSynchronize(e1);
-                float ms = 0.0f;
-                cudaEventElapsedTime(&ms, e0, e1);
+                times[v] = 0.0f;
+                cudaEventElapsedTime(&times[v], e0, e1);
                 count_launch(-5);  // tuning launches are not part of the caller's work
-                if (ms < best) {
-                    best = ms;
-                    pick = v;
-                }
+                if (times[v] < best) best = times[v];
             }
+            for (int v = 0; v < nv; v++)
+                if (times[v] <= best * kTuneSlack) {
+                    pick = v;
+                    break;
+                }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             cudaFree(scratch);
@@ -478,7 +507,7 @@ culgt_status interval_enqueue(culgt_handle *h, int k, int n)
 culgt_status run_interval(culgt_handle *h, int k, int n)
 {
     Mapping m;
-    ST(tuned_mapping(h, &m));
+    if (h->prm.gauge == CULGT_LANDAU) ST(tuned_mapping(h, &m));
     long long mask = 0;
     if (h->prm.reunit_every > 0)
         for (int j = 0; j < k && j < 40; j++)
@@ -817,10 +846,22 @@ culgt_status culgt_handle_fix(culgt_handle *h, culgt_result *out)
 culgt_status culgt_landau_fix(void *d_links, const culgt_params *p, void *cuda_stream, culgt_result *out)
 {
     double t0 = now_seconds();
-    ST(validate(p));
+    ST(validate_landau(p));
     if (!d_links) return CULGT_ERR_ARG;
     HandleGuard g;
     ST(culgt_create(p, cuda_stream, &g.h));
+    return fix_call(g.h, d_links, d_links, out, t0);
+}
+
+culgt_status culgt_mag_fix(void *d_links, const culgt_params *p, void *cuda_stream, culgt_result *out)
+{
+    double t0 = now_seconds();
+    ST(validate(p));
+    if (!d_links) return CULGT_ERR_ARG;
+    culgt_params q = *p;
+    q.gauge = CULGT_MAG;
+    HandleGuard g;
+    ST(culgt_create(&q, cuda_stream, &g.h));
     return fix_call(g.h, d_links, d_links, out, t0);
 }
 
@@ -840,7 +881,7 @@ culgt_status culgt_validate_anneal(const culgt_anneal_params *a) { return valida
 
 culgt_status culgt_handle_heatbath(culgt_handle *h, double T, unsigned long long seed, unsigned sweep_word)
 {
-    if (!h || !h->loaded || !(T > 0.0) || std::isinf(T)) return CULGT_ERR_ARG;
+    if (!h || !h->loaded || !(T > 0.0) || std::isinf(T) || h->prm.gauge != CULGT_LANDAU) return CULGT_ERR_ARG;
     CallScope scope(h);
     ST(heatbath_now(h, T, seed, sweep_word));
     CU(cudaGetLastError());
@@ -849,7 +890,7 @@ culgt_status culgt_handle_heatbath(culgt_handle *h, double T, unsigned long long
 
 culgt_status culgt_handle_heatbath_tuning(culgt_handle *h, int *keep_links, int *min_blocks_per_sm)
 {
-    if (!h || !h->loaded || !keep_links || !min_blocks_per_sm) return CULGT_ERR_ARG;
+    if (!h || !h->loaded || !keep_links || !min_blocks_per_sm || h->prm.gauge != CULGT_LANDAU) return CULGT_ERR_ARG;
     CallScope scope(h);
     int v;
     ST(tuned_heatbath(h, &v));
@@ -859,7 +900,7 @@ culgt_status culgt_handle_heatbath_tuning(culgt_handle *h, int *keep_links, int 
 
 culgt_status culgt_handle_anneal(culgt_handle *h, const culgt_anneal_params *a)
 {
-    if (!h || !h->loaded) return CULGT_ERR_ARG;
+    if (!h || !h->loaded || h->prm.gauge != CULGT_LANDAU) return CULGT_ERR_ARG;
     ST(validate_anneal(a));
     CallScope scope(h);
     return anneal_now(h, a);
@@ -869,7 +910,7 @@ culgt_status culgt_landau_fix_anneal(void *d_links, const culgt_params *p, const
                                      void *cuda_stream, culgt_result *out)
 {
     double t0 = now_seconds();
-    ST(validate(p));
+    ST(validate_landau(p));
     ST(validate_anneal(a));
     if (!d_links) return CULGT_ERR_ARG;
     HandleGuard g;
@@ -880,7 +921,7 @@ culgt_status culgt_landau_fix_anneal(void *d_links, const culgt_params *p, const
 culgt_status culgt_landau_fix_host(void *h_links, const culgt_params *p, void *cuda_stream, culgt_result *out)
 {
     double t0 = now_seconds();
-    ST(validate(p));
+    ST(validate_landau(p));
     if (!h_links) return CULGT_ERR_ARG;
     HandleGuard g;
     ST(culgt_create(p, cuda_stream, &g.h));

@@ -422,6 +422,7 @@ culgt_status fix_batched(const culgt_problem *problems, int n, const culgt_param
         for (int mu = 0; mu < 4; mu++) p.dims[mu] = problems[i].dims[mu];
         culgt_status st = culgt_validate(&p);
         if (st != CULGT_OK) return st;
+        if (p.gauge != CULGT_LANDAU) return CULGT_ERR_ARG;
         if (!problems[i].d_links) return CULGT_ERR_ARG;
     }
     if (cudaStreamSynchronize((cudaStream_t)cuda_stream) != cudaSuccess) {
@@ -483,6 +484,7 @@ extern "C" culgt_status culgt_landau_fix_gauge(void *d_links, const culgt_params
     double t0 = wall_now();
     culgt_status st = culgt_validate(p);
     if (st != CULGT_OK) return st;
+    if (p->gauge != CULGT_LANDAU) return CULGT_ERR_ARG;
     if (!d_links || !d_gauge) return CULGT_ERR_ARG;
     if (cudaStreamSynchronize((cudaStream_t)cuda_stream) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -526,6 +528,7 @@ extern "C" culgt_status culgt_coulomb_fix(void *d_links, const culgt_params *p, 
     double t0 = wall_now();
     culgt_status st = culgt_validate(p);
     if (st != CULGT_OK) return st;
+    if (p->gauge != CULGT_LANDAU) return CULGT_ERR_ARG;
     if (!d_links) return CULGT_ERR_ARG;
     if (cudaStreamSynchronize((cudaStream_t)cuda_stream) != cudaSuccess) {
         (void)cudaGetLastError();

@@ -42,6 +42,12 @@ struct Ops {
                      uint32_t sweep, int variant, cudaStream_t s);
     int heatbath_variants;
     void (*heatbath_mapping)(int variant, int *keep_links, int *min_blocks_per_sm);
+    // one maximally Abelian gauge half-sweep (1 thread per site, blocks of
+    // 128); gacc as in halfsweep
+    void (*mag_halfsweep)(void *base, void *gacc, const Geom &g, int parity, double omega, int variant,
+                          cudaStream_t s);
+    // per-block partial sums of (theta_MAG site terms, sum_mu sum_a |U_aa|^2); returns the block count
+    int (*mag_theta_partials)(const void *base, const Geom &g, double2 *partials, cudaStream_t s);
     // per-block partial sums of (tr Delta Delta^+, sum Re tr U) over all sites; returns the block count
     int (*theta_partials)(const void *base, const Geom &g, int mu_first, double2 *partials, cudaStream_t s);
     // per-block partial sums of the plaquette trace; returns the block count

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "anneal.cuh"
+#include "mag.cuh"
 #include "launch.h"
 
 namespace culgt {
@@ -78,6 +79,21 @@ template <class P> struct OpsImpl {
         *keep_links = m.keep;
         *min_blocks_per_sm = m.minb;
     }
+    static void mag_halfsweep(void *base, void *gacc, const Geom &g, int parity, double omega, int variant,
+                              cudaStream_t s)
+    {
+        typedef typename GaugeParam<P>::type PG;
+        k_mag_halfsweep<P, PG><<<blocks_for(g.Vh, 128), 128, 0, s>>>(
+            (C *)base, (typename PG::Chunk *)gacc, g, parity, (typename P::Real)omega, variant, gacc != nullptr);
+        count_launch();
+    }
+    static int mag_theta_partials(const void *base, const Geom &g, double2 *partials, cudaStream_t s)
+    {
+        unsigned nb = blocks_for(2LL * g.Vh, kThetaThreads);
+        k_mag_theta<P><<<nb, kThetaThreads, 0, s>>>((const C *)base, g, partials);
+        count_launch();
+        return (int)nb;
+    }
     static int theta_partials(const void *base, const Geom &g, int mu_first, double2 *partials, cudaStream_t s)
     {
         unsigned nb = blocks_for(2LL * g.Vh, kThetaThreads);
@@ -150,6 +166,8 @@ template <class P> struct OpsImpl {
         o.heatbath_variants = HbMappings<P>::count;
         o.heatbath_mapping = heatbath_mapping;
         o.theta_partials = theta_partials;
+        o.mag_halfsweep = mag_halfsweep;
+        o.mag_theta_partials = mag_theta_partials;
         o.plaq_partials = plaq_partials;
         o.reunitarize = reunitarize;
         o.gauge_identity = kFP32 ? gauge_identity : nullptr;

@@ -119,6 +119,7 @@ extern "C" culgt_status culgt_theta_static_scratch(const void *d_links, const cu
 {
     culgt_status st = culgt_validate(p);
     if (st != CULGT_OK) return st;
+    if (p->gauge != CULGT_LANDAU) return CULGT_ERR_ARG;
     if (!d_links || !d_out) return CULGT_ERR_ARG;
     long long V = (long long)p->dims[0] * p->dims[1] * p->dims[2] * p->dims[3];
     if (V > kMaxSites) return CULGT_ERR_TOO_LARGE;

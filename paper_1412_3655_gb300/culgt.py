@@ -21,6 +21,7 @@ OK, NOT_CONVERGED = 0, 1
 ERR_ARG, ERR_DIMS, ERR_NC, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_TIMEOUT = -1, -2, -3, -4, -5, -6, -7
 ERR_TOO_LARGE = -8
 FP64, FP32, MIXED, MIXED_DF, DF = 0, 1, 2, 3, 4
+LANDAU, MAG = 0, 1
 
 
 class CulgtError(RuntimeError):
@@ -46,6 +47,7 @@ class _Params(ctypes.Structure):
         ("threads_per_site", ctypes.c_int),
         ("block_size", ctypes.c_int),
         ("min_blocks_per_sm", ctypes.c_int),
+        ("gauge", ctypes.c_int),
     ]
 
 
@@ -110,6 +112,7 @@ class Params:
     threads_per_site: int = 0
     block_size: int = 0
     min_blocks_per_sm: int = 0
+    gauge: int = LANDAU
 
     @classmethod
     def defaults(cls, nc, dims, **kw):
@@ -176,6 +179,7 @@ def library():
                                      ctypes.POINTER(ctypes.c_int)]),
         "culgt_landau_fix": (ip, [vp, P, vp, R]),
         "culgt_landau_fix_host": (ip, [vp, P, vp, R]),
+        "culgt_mag_fix": (ip, [vp, P, vp, R]),
         "culgt_sweep": (ip, [vp, P, ip, vp]),
         "culgt_theta": (ip, [vp, P, vp, dp, dp]),
         "culgt_plaquette": (ip, [vp, P, vp, dp]),
@@ -264,6 +268,15 @@ def culgt_landau_fix(links, params: Params, stream=None) -> Result:
     r = _Result()
     st = _check(library().culgt_landau_fix(_links_ptr(links, params, True), ctypes.byref(params._c()),
                                            _stream(stream), ctypes.byref(r)), "culgt_landau_fix")
+    return Result._from(r, st)
+
+
+def culgt_mag_fix(links, params: Params, stream=None) -> Result:
+    """Maximally Abelian gauge fixing in place (theta and F of the result are
+    theta_MAG and F_MAG)."""
+    r = _Result()
+    st = _check(library().culgt_mag_fix(_links_ptr(links, params, True), ctypes.byref(params._c()), _stream(stream),
+                                        ctypes.byref(r)), "culgt_mag_fix")
     return Result._from(r, st)
 
 

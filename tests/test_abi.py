@@ -143,3 +143,20 @@ def test_anneal_null_arguments_rejected(lib):
     assert so.culgt_handle_anneal(None, ctypes.byref(a._c())) == lib.ERR_ARG
     assert so.culgt_handle_heatbath(None, 1.0, 0, 0) == lib.ERR_ARG
     assert so.culgt_default_anneal_params(None) == lib.ERR_ARG
+
+
+def test_gauge_field_validates(lib):
+    p = lib.Params.defaults(3, (4, 4, 4, 4), gauge=lib.MAG)
+    assert lib.culgt_validate(p) == lib.OK
+    p.gauge = 2
+    assert lib.culgt_validate(p) == lib.ERR_ARG
+    # Landau-only entry points refuse a MAG parameter block before any device work
+    so = lib.library()
+    q = lib.Params.defaults(3, (4, 4, 4, 4), gauge=lib.MAG)
+    assert so.culgt_landau_fix(ctypes.c_void_p(16), ctypes.byref(q._c()), None, None) == lib.ERR_ARG
+    assert so.culgt_landau_fix_host(ctypes.c_void_p(16), ctypes.byref(q._c()), None, None) == lib.ERR_ARG
+    assert so.culgt_coulomb_fix(ctypes.c_void_p(16), ctypes.byref(q._c()), None, None, None) == lib.ERR_ARG
+    a = lib.AnnealParams()
+    assert so.culgt_landau_fix_anneal(ctypes.c_void_p(16), ctypes.byref(q._c()), ctypes.byref(a._c()), None,
+                                      None) == lib.ERR_ARG
+    assert so.culgt_mag_fix(None, ctypes.byref(q._c()), None, None) == lib.ERR_ARG
