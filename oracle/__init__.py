@@ -75,6 +75,7 @@ def _load():
         "oracle_mag_fix": (i, [dp, ip, i, d, i, d, i, i, i, ip, dp, dp]),
         "oracle_mag_local_gauge": (None, [dp, i, d, i, dp]),
         "oracle_mag_su2_max": (None, [dp, dp]),
+        "oracle_coulomb_fix_anneal": (i, [dp, ip, i, d, d, i, i, u32p, d, i, d, i, i, i, dp, ip, dp, dp]),
         "oracle_set_threads": (None, [i]),
         "oracle_get_threads": (i, []),
     }
@@ -320,3 +321,21 @@ def mag_su2_max(Z):
     B = np.zeros((2, 2), dtype=np.complex128)
     _load().oracle_mag_su2_max(_dp(Z), _dp(B))
     return B
+
+
+def coulomb_fix_anneal(U, L, nc, t_start, t_end, steps, n_micro, seed, omega, theta_target, max_sweeps,
+                       check_every=1, reunit_every=0, variant=0):
+    """Coulomb gauge fixing with every time slice annealed first (slice t keyed
+    by seed + t). Returns the dict of coulomb_fix."""
+    _check_links(U, L, nc)
+    V = int(np.prod(L))
+    g = np.zeros((V, nc, nc), dtype=np.complex128)
+    nt = int(L[0])
+    sw = (ctypes.c_int * nt)()
+    th = np.zeros(nt)
+    F = np.zeros(nt)
+    rc = _load().oracle_coulomb_fix_anneal(_dp(U), _dims(L), nc, float(t_start), float(t_end), int(steps),
+                                           int(n_micro), _key(seed), float(omega), int(variant), float(theta_target),
+                                           int(max_sweeps), int(check_every), int(reunit_every), _dp(g), sw, _dp(th),
+                                           _dp(F))
+    return {"converged": rc == 0, "sweeps": np.array(list(sw)), "theta": th, "F": F, "g": g}

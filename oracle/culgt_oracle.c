@@ -643,14 +643,49 @@ static void slice_reunitarize(double *U, const lattice *lat, int nc, int t, doub
     }
 }
 
+static void heatbath_site(double *U, const lattice *lat, int nc, long i, int mu_first, double inv_T,
+                          const uint32_t *key, uint32_t sweep, double *gacc);
+
+/* Annealing of one time slice before its overrelaxation (the schedule of
+ * R11 on the slice's spatial links, with its checkerboard; draws keyed by
+ * key_t, g accumulated into gacc). */
+static void slice_anneal(double *U, const lattice *lat, int nc, int t, double t_start, double t_end, int steps,
+                         int n_micro, const uint32_t *key_t, int reunit_every, double *gacc)
+{
+    long V3 = (long)lat->L[1] * lat->L[2] * lat->L[3];
+    long done = 0;
+    for (int k = 0; k < steps; k++) {
+        double T = steps > 1 ? t_start + (t_end - t_start) * (double)k / (double)(steps - 1) : t_start;
+        double inv_T = 1.0 / T;
+        for (int m = 0; m <= n_micro; m++) {
+            for (int parity = 0; parity < 2; parity++) {
+                if (m == 0) {
+#pragma omp parallel for schedule(static)
+                    for (long j = 0; j < V3; j++) {
+                        long i = slice_site(lat, t, j);
+                        if (site_parity(lat, i, 1) == parity)
+                            heatbath_site(U, lat, nc, i, 1, inv_T, key_t, (uint32_t)k, gacc);
+                    }
+                } else {
+                    slice_halfsweep(U, lat, nc, t, parity, 2.0, 0, gacc);
+                }
+            }
+            done++;
+            if (reunit_every > 0 && done % reunit_every == 0) slice_reunitarize(U, lat, nc, t, gacc);
+        }
+    }
+}
+
 /* Coulomb gauge fixing: every slice t runs the Landau iteration above on its
  * spatial links alone and stops at its own theta_t; the accumulated g(x) then
  * rotates the temporal links, U_0(x) <- g(x) U_0(x) g(x+0)^+. gacc (V Nc Nc
  * complex) receives the accumulated transformation. Per-slice outputs have
- * L[0] entries. Returns 0 if every slice converged. */
-int oracle_coulomb_fix(double *U, const int *L, int nc, double omega, int variant, double theta_target,
+ * L[0] entries. With anneal != NULL (t_start, t_end, steps, n_micro) every
+ * slice is first annealed, slice t drawing with the key seed + t. Returns 0
+ * if every slice converged. */
+static int coulomb_run(double *U, const int *L, int nc, double omega, int variant, double theta_target,
                        int max_sweeps, int check_every, int reunit_every, double *gacc, int *sweeps_t,
-                       double *theta_t, double *F_t)
+                       double *theta_t, double *F_t, const double *anneal, uint64_t seed)
 {
     lattice lat = make_lattice(L);
     int all_ok = 1;
@@ -659,6 +694,12 @@ int oracle_coulomb_fix(double *U, const int *L, int nc, double omega, int varian
         put_mat(gacc, nc, i, &I);
     }
     for (int t = 0; t < L[0]; t++) {
+        if (anneal) {
+            uint64_t kt = seed + (uint64_t)t;
+            uint32_t key_t[2] = {(uint32_t)kt, (uint32_t)(kt >> 32)};
+            slice_anneal(U, &lat, nc, t, anneal[0], anneal[1], (int)anneal[2], (int)anneal[3], key_t, reunit_every,
+                         gacc);
+        }
         double th, F;
         int n = 0;
         oracle_theta_slice(U, L, nc, t, &th, &F);
@@ -687,6 +728,26 @@ int oracle_coulomb_fix(double *U, const int *L, int nc, double omega, int varian
         put_link(U, nc, i, 0, &t);
     }
     return all_ok ? 0 : 1;
+}
+
+int oracle_coulomb_fix(double *U, const int *L, int nc, double omega, int variant, double theta_target,
+                       int max_sweeps, int check_every, int reunit_every, double *gacc, int *sweeps_t,
+                       double *theta_t, double *F_t)
+{
+    return coulomb_run(U, L, nc, omega, variant, theta_target, max_sweeps, check_every, reunit_every, gacc,
+                       sweeps_t, theta_t, F_t, NULL, 0);
+}
+
+/* Coulomb gauge fixing with every slice annealed first (R11 per slice). */
+int oracle_coulomb_fix_anneal(double *U, const int *L, int nc, double t_start, double t_end, int steps, int n_micro,
+                              const uint32_t *key, double omega, int variant, double theta_target, int max_sweeps,
+                              int check_every, int reunit_every, double *gacc, int *sweeps_t, double *theta_t,
+                              double *F_t)
+{
+    double a[4] = {t_start, t_end, (double)steps, (double)n_micro};
+    uint64_t seed = (uint64_t)key[0] | ((uint64_t)key[1] << 32);
+    return coulomb_run(U, L, nc, omega, variant, theta_target, max_sweeps, check_every, reunit_every, gacc,
+                       sweeps_t, theta_t, F_t, a, seed);
 }
 
 /* ------------------------------------------------------------------ */
@@ -875,13 +936,13 @@ static mat heatbath_gauge(const mat *K, double inv_T, const uint32_t *key, uint3
     return g;
 }
 
-static void heatbath_site(double *U, const lattice *lat, int nc, long i, double inv_T, const uint32_t *key,
-                          uint32_t sweep, double *gacc)
+static void heatbath_site(double *U, const lattice *lat, int nc, long i, int mu_first, double inv_T,
+                          const uint32_t *key, uint32_t sweep, double *gacc)
 {
-    mat K = gather_K(U, lat, nc, i, 0);
+    mat K = gather_K(U, lat, nc, i, mu_first);
     mat g = heatbath_gauge(&K, inv_T, key, (uint32_t)i, sweep);
     mat gd = mat_adj(&g);
-    for (int mu = 0; mu < 4; mu++) {
+    for (int mu = mu_first; mu < 4; mu++) {
         long ib = site_shift(lat, i, mu, -1);
         mat f = get_link(U, nc, i, mu);
         mat b = get_link(U, nc, ib, mu);
@@ -907,7 +968,7 @@ void oracle_heatbath_halfsweep(double *U, const int *L, int nc, int parity, doub
     double inv_T = 1.0 / T;
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < lat.V; i++)
-        if (site_parity(&lat, i, 0) == parity) heatbath_site(U, &lat, nc, i, inv_T, key, sweep, gacc);
+        if (site_parity(&lat, i, 0) == parity) heatbath_site(U, &lat, nc, i, 0, inv_T, key, sweep, gacc);
 }
 
 void oracle_heatbath_sweep(double *U, const int *L, int nc, double T, const uint32_t *key, uint32_t sweep,

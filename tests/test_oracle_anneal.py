@@ -268,3 +268,45 @@ def test_heatbath_sweep_draws_with_the_site_and_sweep_words(orc, nc):
         assert np.abs(h[i, 0] - g @ U[i, 0]).max() < 1e-14
         g_other = orc.heatbath_gauge(K, 0.8, 41, int(i) ^ 1, 6)
         assert np.abs(g_other - g).max() > 1e-3
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_coulomb_anneal_without_steps_is_coulomb_fix(orc, nc):
+    dims = (4, 4, 4, 2)
+    U = synth.gauge_config(dims, nc, 0.3, 5)
+    a = U.copy()
+    ra = orc.coulomb_fix_anneal(a, dims, nc, 0.6, 0.05, 0, 2, 9, 1.7, 1e-12, 3000, 5, 25)
+    b = U.copy()
+    rb = orc.coulomb_fix(b, dims, nc, 1.7, 1e-12, 3000, 5, 25)
+    assert np.array_equal(a, b) and np.array_equal(ra["g"], rb["g"])
+    assert list(ra["sweeps"]) == list(rb["sweeps"])
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_coulomb_anneal_is_one_gauge_transformation(orc, nc):
+    """Annealing then overrelaxing every slice: the output is the input
+    transformed by the returned g (spatial links rotated on the way, temporal
+    links once at the end), every slice converges, the plaquette stays."""
+    dims = (4, 4, 4, 2)
+    U = synth.gauge_config(dims, nc, 0.5, 6)
+    out = U.copy()
+    r = orc.coulomb_fix_anneal(out, dims, nc, 0.6, 0.05, 20, 2, 9, 1.7, 1e-12, 5000, 5, 25)
+    assert r["converged"] and (r["theta"] < 1e-12).all()
+    assert np.abs(out - synth.gauge_transform(U, dims, r["g"])).max() < 1e-12
+    assert orc.plaquette(out, dims, nc) == pytest.approx(orc.plaquette(U, dims, nc), abs=1e-12)
+    for t in range(dims[0]):
+        th, F = orc.theta_slice(out, dims, nc, t)
+        assert th == pytest.approx(r["theta"][t], rel=1e-12) and F == pytest.approx(r["F"][t], rel=1e-14)
+
+
+def test_coulomb_annealing_raises_the_slice_maxima(orc):
+    """Rough field (eps 0.6): over 8 gauge copies the annealed slices end on
+    larger maxima of F_t on average than overrelaxation alone."""
+    dims = (2, 4, 4, 4)
+    plain, ann = [], []
+    for c in range(8):
+        U = synth.gauge_config(dims, 3, 0.6, 3, copy=c)
+        plain += list(orc.coulomb_fix(U.copy(), dims, 3, 1.7, 1e-12, 20000, 10, 50)["F"])
+        ann += list(orc.coulomb_fix_anneal(U.copy(), dims, 3, 0.6, 0.01, 200, 3, 40 + c, 1.7, 1e-12, 20000, 10,
+                                           50)["F"])
+    assert np.mean(ann) > np.mean(plain)
