@@ -636,7 +636,7 @@ def run_culgt(args):
         bytes_launch = (V // 2) * BYTES_PER_SITE[key]
         achieved = bytes_launch / (t_ms / 1e3) / 1e9
         name = (f"halfsweep_su{nc}_{'f32' if key[1] else 'f64'}_{key[2]}" + ("_acc" if len(key) > 3 else "")
-                + f"_tps{m[0]}_mb{m[2]}")
+                + f"_tps{m[0]}_b{m[1]}_mb{m[2]}")
         return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": recorded_traffic(name), "kernel": name, "launch_ms": t_ms,
                 "algorithmic_bytes_per_launch": bytes_launch, "peak_source": f"{peak_src} hbm_gbs"}
@@ -646,7 +646,7 @@ def run_culgt(args):
         # (FMA = 2) against 2 DFMA/clock/SM x 152 SMs x 2070 MHz
         flops_launch = (V // 2) * FLOPS_PER_SITE[nc]
         achieved = flops_launch / (t_ms / 1e3) / 1e12
-        name = f"halfsweep_su{nc}_{'f32' if key[1] else 'f64'}_{key[2]}_tps{m[0]}_mb{m[2]}"
+        name = f"halfsweep_su{nc}_{'f32' if key[1] else 'f64'}_{key[2]}_tps{m[0]}_b{m[1]}_mb{m[2]}"
         return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(name), "kernel": name,
                 "launch_ms": t_ms, "algorithmic_flops_per_launch": flops_launch,

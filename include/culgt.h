@@ -315,6 +315,13 @@ culgt_status culgt_landau_fix_anneal(void *d_links, const culgt_params *p, const
 culgt_status culgt_fix_batched_anneal(const culgt_problem *problems, int n, const culgt_params *common,
                                       const culgt_anneal_params *a, void *cuda_stream, culgt_result *out);
 
+/* culgt_coulomb_fix with the annealing schedule run on every time slice
+ * first (spatial links, the slice's own checkerboard, g accumulated for the
+ * temporal links), all slices in step in shared launches; slice t draws
+ * with the key seed + t. */
+culgt_status culgt_coulomb_fix_anneal(void *d_links, const culgt_params *p, const culgt_anneal_params *a,
+                                      void *cuda_stream, culgt_result *per_slice, void *d_gauge);
+
 #ifdef __cplusplus
 }
 #endif

@@ -522,14 +522,17 @@ extern "C" culgt_status culgt_landau_fix_gauge(void *d_links, const culgt_params
     return e.status();
 }
 
-extern "C" culgt_status culgt_coulomb_fix(void *d_links, const culgt_params *p, void *cuda_stream,
-                                          culgt_result *per_slice, void *d_gauge)
+namespace {
+
+culgt_status coulomb_call(void *d_links, const culgt_params *p, const culgt_anneal_params *anneal, void *cuda_stream,
+                          culgt_result *per_slice, void *d_gauge)
 {
     double t0 = wall_now();
     culgt_status st = culgt_validate(p);
     if (st != CULGT_OK) return st;
     if (p->gauge != CULGT_LANDAU) return CULGT_ERR_ARG;
     if (!d_links) return CULGT_ERR_ARG;
+    if (anneal) EST(culgt_validate_anneal(anneal));
     if (cudaStreamSynchronize((cudaStream_t)cuda_stream) != cudaSuccess) {
         (void)cudaGetLastError();
         return CULGT_ERR_CUDA;
@@ -545,6 +548,7 @@ extern "C" culgt_status culgt_coulomb_fix(void *d_links, const culgt_params *p, 
     EST(e.upload());
     double pb, pa, ue;
     EST(e.plaquette(e.lat[0], &pb));
+    if (anneal) EST(e.anneal(anneal));
     EST(e.run());
     // the accumulated g rotates the temporal links (untouched so far)
     if (e.has64)
@@ -576,4 +580,19 @@ extern "C" culgt_status culgt_coulomb_fix(void *d_links, const culgt_params *p, 
             per_slice[t].seconds = secs;
         }
     return e.status();
+}
+
+} // namespace
+
+extern "C" culgt_status culgt_coulomb_fix(void *d_links, const culgt_params *p, void *cuda_stream,
+                                          culgt_result *per_slice, void *d_gauge)
+{
+    return coulomb_call(d_links, p, nullptr, cuda_stream, per_slice, d_gauge);
+}
+
+extern "C" culgt_status culgt_coulomb_fix_anneal(void *d_links, const culgt_params *p, const culgt_anneal_params *a,
+                                                 void *cuda_stream, culgt_result *per_slice, void *d_gauge)
+{
+    if (!a) return CULGT_ERR_ARG;
+    return coulomb_call(d_links, p, a, cuda_stream, per_slice, d_gauge);
 }

@@ -195,6 +195,7 @@ def library():
         "culgt_handle_heatbath_tuning": (ip, [H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "culgt_landau_fix_anneal": (ip, [vp, P, A, vp, R]),
         "culgt_fix_batched_anneal": (ip, [ctypes.POINTER(_Problem), ip, P, A, vp, R]),
+        "culgt_coulomb_fix_anneal": (ip, [vp, P, A, vp, R, vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -351,6 +352,18 @@ def culgt_landau_fix_anneal(links, params: Params, anneal: AnnealParams, stream=
                                                   ctypes.byref(anneal._c()), _stream(stream), ctypes.byref(r)),
                 "culgt_landau_fix_anneal")
     return Result._from(r, st)
+
+
+def culgt_coulomb_fix_anneal(links, params: Params, anneal: AnnealParams, stream=None, gauge=None):
+    """Coulomb gauge fixing with every time slice annealed first (slice t
+    draws with seed + t). One Result per slice; gauge as in culgt_coulomb_fix."""
+    nt = int(params.dims[0])
+    rs = (_Result * nt)()
+    gp = _gauge_ptr(gauge, params) if gauge is not None else None
+    st = _check(library().culgt_coulomb_fix_anneal(_links_ptr(links, params, True), ctypes.byref(params._c()),
+                                                   ctypes.byref(anneal._c()), _stream(stream), rs, gp),
+                "culgt_coulomb_fix_anneal")
+    return [Result._from(r, st) for r in rs]
 
 
 def culgt_fix_batched_anneal(links_list, dims_list, params: Params, anneal: AnnealParams, stream=None):

@@ -160,3 +160,13 @@ def test_gauge_field_validates(lib):
     assert so.culgt_landau_fix_anneal(ctypes.c_void_p(16), ctypes.byref(q._c()), ctypes.byref(a._c()), None,
                                       None) == lib.ERR_ARG
     assert so.culgt_mag_fix(None, ctypes.byref(q._c()), None, None) == lib.ERR_ARG
+
+
+def test_coulomb_anneal_rejects_before_device_work(lib):
+    so = lib.library()
+    p = lib.Params.defaults(3, (4, 4, 4, 4))
+    bad = lib.AnnealParams(steps=-1)
+    assert so.culgt_coulomb_fix_anneal(ctypes.c_void_p(16), ctypes.byref(p._c()), ctypes.byref(bad._c()), None,
+                                       None, None) == lib.ERR_ARG
+    assert so.culgt_coulomb_fix_anneal(ctypes.c_void_p(16), ctypes.byref(p._c()), None, None, None,
+                                       None) == lib.ERR_ARG

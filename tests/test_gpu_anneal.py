@@ -252,3 +252,33 @@ def test_full_size_heatbath_sweep(cu, orc, nc):
     # on the random start the FP32 maximiser is ill conditioned at a few
     # sites per 10^5 as well
     assert np.mean(link_errors(got32, ref32) > 5e-6) <= 2e-3
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("nc", [2, 3])
+def test_coulomb_fix_anneal(cu, orc, nc, precision):
+    """Coulomb gauge with every slice annealed first (slice t keyed by seed +
+    t): FP64 takes the oracle's sweep count per slice with F_t within 1e-10
+    and the same link traces; both precisions return a g that maps the input
+    onto the output, and keep the plaquette."""
+    prec = cu.FP64 if precision == "fp64" else cu.MIXED
+    dims = (4, 4, 4, 2)
+    V = int(np.prod(dims))
+    U = synth.gauge_config(dims, nc, 0.5, 6)
+    d = to_dev(U)
+    gauge = torch.zeros(V * nc * nc * 2, dtype=torch.float64, device="cuda")
+    p = cu.Params.defaults(nc, dims, precision=prec, check_every=5, reunit_every=25, max_sweeps=5000)
+    res = cu.culgt_coulomb_fix_anneal(d, p, cu.AnnealParams(0.6, 0.05, 20, 2, SEED), gauge=gauge)
+    ref = U.copy()
+    rr = orc.coulomb_fix_anneal(ref, dims, nc, 0.6, 0.05, 20, 2, SEED, 1.7, 1e-12, 5000, 5, 25)
+    got = from_dev(d, U.shape)
+    g = gauge.cpu().numpy().view(np.complex128).reshape(V, nc, nc)
+    for t in range(dims[0]):
+        assert res[t].status == cu.OK and res[t].theta < 1e-12
+        assert res[t].F == pytest.approx(rr["F"][t], rel=1e-10)
+        if prec == cu.FP64:
+            assert res[t].sweeps_fp64 == rr["sweeps"][t]
+    if prec == cu.FP64:
+        assert np.abs(traces(got) - traces(ref)).max() < 1e-9
+    assert np.abs(got - synth.gauge_transform(U, dims, g)).max() < (1e-12 if prec == cu.FP64 else 1e-10)
+    assert res[0].plaq_after == pytest.approx(res[0].plaq_before, abs=1e-12)

@@ -45,7 +45,7 @@ def mag_warmed(U, dims, nc, orc, n=5):
     return W
 
 
-def assert_close(got, ref, tol, well_conditioned):
+def assert_close(got, ref, tol, well_conditioned, q=0.995):
     """Every link within tol on well-conditioned input. On the random Haar
     start, 99.5% of links: the SU(3) block vector z is a difference of sums of
     rank-one projectors, rotated by the earlier subgroup steps, and comes out
@@ -53,13 +53,15 @@ def assert_close(got, ref, tol, well_conditioned):
     (the axis of the maximising rotation amplifies rounding by about
     |X| / (|z| + z3)). Perturbing the oracle's input by 1e-14 on the 6x4x6x10
     SU(3) case moves its MAG output by up to 280x at the 99.9% quantile and
-    61x at 99.5%, against 66x and 35x for the Landau sweep."""
+    61x at 99.5%, against 66x and 35x for the Landau sweep. FP32 (rounding
+    6e-8, so about 4e-6 at that 99.5% amplification before the FP32 sums
+    add theirs) is held to 5e-6 on 99% of the links of the random start."""
     nc = got.shape[-1]
     err = np.abs(got - ref).reshape(-1, nc * nc).max(axis=1)
     if well_conditioned:
         assert err.max() <= tol, f"max {err.max():.3e}"
     else:
-        assert np.quantile(err, 0.995) <= tol, f"q99.5 {np.quantile(err, 0.995):.3e}"
+        assert np.quantile(err, q) <= tol, f"q{100 * q:g} {np.quantile(err, q):.3e}"
         assert err.max() <= 1000 * tol, f"max {err.max():.3e}"
 
 
@@ -91,7 +93,7 @@ def test_one_mag_sweep_fp32(cu, orc, dims, nc):
             d = to_dev(U)
             p = cu.Params.defaults(nc, dims, precision=cu.FP32, storage_reals=sr, gauge=cu.MAG)
             cu.culgt_sweep(d, p, 1)
-            assert_close(from_dev(d, U.shape), ref, 5e-6, good)
+            assert_close(from_dev(d, U.shape), ref, 5e-6, good, q=0.99)
 
 
 @pytest.mark.parametrize("nc", [2, 3])
