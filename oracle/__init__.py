@@ -76,6 +76,10 @@ def _load():
         "oracle_mag_local_gauge": (None, [dp, i, d, i, dp]),
         "oracle_mag_su2_max": (None, [dp, dp]),
         "oracle_coulomb_fix_anneal": (i, [dp, ip, i, d, d, i, i, u32p, d, i, d, i, i, i, dp, ip, dp, dp]),
+        "oracle_mag_heatbath_halfsweep": (None, [dp, ip, i, i, d, u32p, ctypes.c_uint32]),
+        "oracle_mag_heatbath_sweep": (None, [dp, ip, i, d, u32p, ctypes.c_uint32]),
+        "oracle_mag_anneal": (None, [dp, ip, i, d, d, i, i, u32p, i]),
+        "oracle_mag_heatbath_su2": (None, [dp, d, u32p, ctypes.c_uint32, ctypes.c_uint32, i, dp]),
         "oracle_set_threads": (None, [i]),
         "oracle_get_threads": (i, []),
     }
@@ -339,3 +343,28 @@ def coulomb_fix_anneal(U, L, nc, t_start, t_end, steps, n_micro, seed, omega, th
                                            int(max_sweeps), int(check_every), int(reunit_every), _dp(g), sw, _dp(th),
                                            _dp(F))
     return {"converged": rc == 0, "sweeps": np.array(list(sw)), "theta": th, "F": F, "g": g}
+
+
+def mag_heatbath_sweep(U, L, nc, T, seed, sweep):
+    """One MAG heat-bath sweep at temperature T (draw counter word `sweep`), in place."""
+    _check_links(U, L, nc)
+    _load().oracle_mag_heatbath_sweep(_dp(U), _dims(L), nc, float(T), _key(seed), int(sweep))
+
+
+def mag_heatbath_halfsweep(U, L, nc, parity, T, seed, sweep):
+    _check_links(U, L, nc)
+    _load().oracle_mag_heatbath_halfsweep(_dp(U), _dims(L), nc, int(parity), float(T), _key(seed), int(sweep))
+
+
+def mag_anneal(U, L, nc, t_start, t_end, steps, n_micro, seed, reunit_every=0):
+    """The annealing schedule with MAG heat-bath and microcanonical sweeps, in place."""
+    _check_links(U, L, nc)
+    _load().oracle_mag_anneal(_dp(U), _dims(L), nc, float(t_start), float(t_end), int(steps), int(n_micro),
+                              _key(seed), int(reunit_every))
+
+
+def mag_heatbath_su2(Z, T, seed, site, sweep, sub=0):
+    Z = np.ascontiguousarray(Z, dtype=np.complex128)
+    B = np.zeros((2, 2), dtype=np.complex128)
+    _load().oracle_mag_heatbath_su2(_dp(Z), float(T), _key(seed), int(site), int(sweep), int(sub), _dp(B))
+    return B

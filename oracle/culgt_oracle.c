@@ -55,6 +55,9 @@
  *   R14 SU(3): the subgroups of R1, running X_a rotated by every step, each
  *       step overrelaxed as in R3.
  *   R15 theta_MAG = (1/V) sum_x sum_{i != j} |(X_i - X_j)_ij|^2.
+ *   R16 MAG annealing: each subgroup draws B = C Bmax with u = c0^2 + c3^2
+ *       exponential on [0, 1] (rate 2|z|/T), the two residual angles uniform;
+ *       microcanonical sweeps are MAG overrelaxation at omega = 2.
  */
 #include <math.h>
 #include <stddef.h>
@@ -1208,6 +1211,127 @@ void oracle_mag_su2_max(const double *Z, double *B)
 {
     mat z = get_mat(Z, 2, 0);
     mat b = mag_su2_max(&z);
+    put_mat(B, 2, 0, &b);
+}
+
+/* R16: MAG heat bath. For the block vector z (R13) with n = |z| > 0 the
+ * subgroup functional of B = C Bmax (Bmax the maximiser) is n (2u - 1) with
+ * u = c0^2 + c3^2 for C = (c0, c1, c2, c3); under Haar measure u is uniform on
+ * [0, 1], so the weight exp(functional / T) makes u exponential with rate
+ * -beta, beta = 2 n / T, drawn by inversion: w = 1 - u = -log1p(v expm1(-beta)) / beta
+ * and, for beta <= 30, u = log1p((1 - v) expm1(beta)) / beta (else 1 - w).
+ * C = (sqrt(u) cos a, sqrt(w) cos c, sqrt(w) sin c, sqrt(u) sin a) with the
+ * angles a = 2 pi v1, c = 2 pi v2 uniform. Counter (site, sweep, sub << 1, 0),
+ * one Philox block per subgroup. n = 0 leaves the block alone. */
+static mat mag_heatbath_su2(const mat *Z, double inv_T, const uint32_t *key, uint32_t site, uint32_t sweep, int sub)
+{
+    double z3 = 0.5 * (Z->m[0][0].re - Z->m[1][1].re);
+    double z1 = Z->m[0][1].re, z2 = -Z->m[0][1].im;
+    double n = sqrt(z1 * z1 + z2 * z2 + z3 * z3);
+    if (!(n > 0.0)) return mat_identity(2);
+    mat Bmax = mag_su2_max(Z);
+    double beta = (2.0 * n) * inv_T;
+    double v[4];
+    draw4(key, site, sweep, (uint32_t)sub << 1, v);
+    double w = -log1p(v[0] * expm1(-beta)) / beta;
+    double u = beta <= 30.0 ? log1p((1.0 - v[0]) * expm1(beta)) / beta : 1.0 - w;
+    double su = sqrt(u), sw = sqrt(w);
+    double c[4] = {su * cos(TWO_PI * v[1]), sw * cos(TWO_PI * v[2]), sw * sin(TWO_PI * v[2]), su * sin(TWO_PI * v[1])};
+    mat C = quaternion_matrix(c);
+    mat B = mat_mul(&C, &Bmax);
+    cplx s = c_sqrt(mat_det2(&B));
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++) B.m[a][b] = c_div(B.m[a][b], s);
+    return B;
+}
+
+/* the MAG heat-bath site transformation: the subgroups of R14 with the draw of
+ * R16 in place of the overrelaxed maximiser */
+static mat mag_heatbath_gauge(mat *X, int nc, double inv_T, const uint32_t *key, uint32_t site, uint32_t sweep)
+{
+    static const int sub[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    int nsub = nc == 2 ? 1 : 3;
+    mat g = mat_identity(nc);
+    for (int s = 0; s < nsub; s++) {
+        int i = sub[s][0], j = sub[s][1];
+        mat D = mat_sub(&X[i], &X[j]);
+        mat Z = mat_zero(2);
+        Z.m[0][0] = D.m[i][i];
+        Z.m[0][1] = D.m[i][j];
+        Z.m[1][0] = D.m[j][i];
+        Z.m[1][1] = D.m[j][j];
+        mat r = mag_heatbath_su2(&Z, inv_T, key, site, sweep, s);
+        mat R = mat_identity(nc);
+        R.m[i][i] = r.m[0][0];
+        R.m[i][j] = r.m[0][1];
+        R.m[j][i] = r.m[1][0];
+        R.m[j][j] = r.m[1][1];
+        mat Rd = mat_adj(&R);
+        for (int a = 0; a < nc; a++) {
+            mat t = mat_mul(&R, &X[a]);
+            X[a] = mat_mul(&t, &Rd);
+        }
+        g = mat_mul(&R, &g);
+    }
+    return g;
+}
+
+void oracle_mag_heatbath_halfsweep(double *U, const int *L, int nc, int parity, double T, const uint32_t *key,
+                                   uint32_t sweep)
+{
+    lattice lat = make_lattice(L);
+    double inv_T = 1.0 / T;
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < lat.V; i++) {
+        if (site_parity(&lat, i, 0) != parity) continue;
+        mat X[3];
+        mag_X(U, &lat, nc, i, X);
+        mat g = mag_heatbath_gauge(X, nc, inv_T, key, (uint32_t)i, sweep);
+        mat gd = mat_adj(&g);
+        for (int mu = 0; mu < 4; mu++) {
+            long ib = site_shift(&lat, i, mu, -1);
+            mat f = get_link(U, nc, i, mu);
+            mat b = get_link(U, nc, ib, mu);
+            mat fn = mat_mul(&g, &f);
+            mat bn = mat_mul(&b, &gd);
+            put_link(U, nc, i, mu, &fn);
+            put_link(U, nc, ib, mu, &bn);
+        }
+    }
+}
+
+void oracle_mag_heatbath_sweep(double *U, const int *L, int nc, double T, const uint32_t *key, uint32_t sweep)
+{
+    oracle_mag_heatbath_halfsweep(U, L, nc, 0, T, key, sweep);
+    oracle_mag_heatbath_halfsweep(U, L, nc, 1, T, key, sweep);
+}
+
+/* the schedule of R11 with MAG heat-bath sweeps and MAG microcanonical sweeps
+ * (omega = 2: the smallest rotation applied twice keeps each block functional) */
+void oracle_mag_anneal(double *U, const int *L, int nc, double t_start, double t_end, int steps, int n_micro,
+                       const uint32_t *key, int reunit_every)
+{
+    lattice lat = make_lattice(L);
+    long done = 0;
+    for (int k = 0; k < steps; k++) {
+        double T = steps > 1 ? t_start + (t_end - t_start) * (double)k / (double)(steps - 1) : t_start;
+        for (int m = 0; m <= n_micro; m++) {
+            if (m == 0)
+                oracle_mag_heatbath_sweep(U, L, nc, T, key, (uint32_t)k);
+            else
+                oracle_mag_sweep(U, L, nc, 2.0, 0, 1);
+            done++;
+            if (reunit_every > 0 && done % reunit_every == 0) oracle_reunitarize(U, lat.V * 4, nc);
+        }
+    }
+}
+
+/* one MAG heat-bath subgroup draw for a 2x2 hermitian block Z */
+void oracle_mag_heatbath_su2(const double *Z, double T, const uint32_t *key, uint32_t site, uint32_t sweep, int sub,
+                             double *B)
+{
+    mat z = get_mat(Z, 2, 0);
+    mat b = mag_heatbath_su2(&z, 1.0 / T, key, site, sweep, sub);
     put_mat(B, 2, 0, &b);
 }
 

@@ -244,3 +244,108 @@ def test_su2_site_update_is_the_overrelaxed_maximiser(orc, omega, variant):
     gw, _ = orc.mag_local_gauge(X, omega, variant)
     assert np.abs(gw - orc.overrelax(g1, omega, variant)).max() < 1e-14
     assert np.abs(gw - g1).max() > 1e-3
+
+
+# ---------------------------------------------------------------- MAG annealing (R16)
+
+
+def _u_cdf(beta):
+    return lambda u: np.expm1(beta * np.clip(u, 0, 1)) / np.expm1(beta)
+
+
+@pytest.mark.parametrize("T", [50.0, 3.0, 0.5, 0.05])
+def test_mag_heatbath_draw_follows_the_boltzmann_weight(orc, T):
+    """For a fixed block Z with |z| = n the drawn B has the subgroup functional
+    (1/2) tr[s3 B Z B^+] = n (2u - 1), u exponential on [0, 1] with rate
+    2n/T (Haar measure makes u uniform); the residual angles of C = B Bmax^+
+    are uniform."""
+    from scipy import stats
+    rng = np.random.default_rng(40)
+    Z = random_hermitian(2, rng)
+    n = np.linalg.norm([Z[0, 1].real, Z[0, 1].imag, 0.5 * (Z[0, 0] - Z[1, 1]).real])
+    Bmax = orc.mag_su2_max(Z)
+    N = 8000
+    Bs = np.array([orc.mag_heatbath_su2(Z, T, 3, s, 1, s % 3) for s in range(N)])
+    f = 0.5 * np.einsum("ij,njk,kl,nil->n", S3, Bs, Z, Bs.conj()).real
+    u = (f / n + 1) / 2
+    beta = 2 * n / T
+    assert stats.kstest(u, _u_cdf(beta)).pvalue > 1e-3
+    C = Bs @ Bmax.conj().T
+    c0, c3 = C[:, 0, 0].real, C[:, 0, 0].imag
+    c2, c1 = C[:, 0, 1].real, C[:, 0, 1].imag
+    assert np.abs(c0 ** 2 + c3 ** 2 - u).max() < 1e-12
+    for ang in (np.arctan2(c3, c0), np.arctan2(c2, c1)):
+        ok = np.hypot(np.cos(ang), np.sin(ang)) > 0
+        assert stats.kstest((ang[ok] + np.pi) / (2 * np.pi), "uniform").pvalue > 1e-3
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_zero_temperature_mag_heatbath_is_the_maximisation_up_to_U1(orc, nc):
+    """T -> 0 draws u = 1: B = e^{i a s3} Bmax, the maximiser up to the
+    diagonal rotation MAG leaves free, so the moduli |U_ab| of the links and
+    F_MAG equal those after an omega = 1 MAG sweep."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_config(dims, nc, 0.3, 9)
+    a = U.copy()
+    orc.mag_heatbath_sweep(a, dims, nc, 1e-24, 5, 0)
+    b = U.copy()
+    orc.mag_sweep(b, dims, nc, 1.0, 1)
+    assert np.abs(np.abs(a) - np.abs(b)).max() < 1e-9
+    assert orc.mag_theta(a, dims, nc)[1] == pytest.approx(orc.mag_theta(b, dims, nc)[1], abs=1e-12)
+    assert np.abs(a - b).max() > 1e-3  # the diagonal rotations are drawn
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_infinite_temperature_mag_heatbath_is_haar(orc, nc):
+    """T -> infinity: g(x) Haar, E|(g U h^+)_aa|^2 = 1/Nc, so F_MAG -> 1/Nc."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_config(dims, nc, 0.3, 10)
+    orc.mag_heatbath_sweep(U, dims, nc, 1e9, 6, 0)
+    F = orc.mag_theta(U, dims, nc)[1]
+    n = 4 * int(np.prod(dims)) * nc
+    assert abs(F - 1.0 / nc) < 6 * 0.5 / np.sqrt(n)
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_mag_microcanonical_sweep_keeps_F(orc, nc):
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_config(dims, nc, 0.3, 11)
+    F0 = orc.mag_theta(U, dims, nc)[1]
+    orc.mag_sweep(U, dims, nc, 2.0, 1)
+    assert orc.mag_theta(U, dims, nc)[1] == pytest.approx(F0, abs=1e-13)
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_mag_anneal_schedule(orc, nc):
+    dims = (2, 4, 2, 4)
+    U = synth.gauge_config(dims, nc, 0.3, 12)
+    a = U.copy()
+    orc.mag_anneal(a, dims, nc, 1.0, 0.1, 3, 2, 17)
+    b = U.copy()
+    for k in range(3):
+        orc.mag_heatbath_sweep(b, dims, nc, 1.0 + (0.1 - 1.0) * k / 2, 17, k)
+        orc.mag_sweep(b, dims, nc, 2.0, 2)
+    assert np.array_equal(a, b)
+
+
+def test_mag_annealing_then_overrelaxation_finds_higher_maxima(orc):
+    dims = (4, 4, 4, 4)
+    plain, ann = [], []
+    for c in range(6):
+        U = synth.gauge_config(dims, 3, 0.6, 1, copy=c)
+        plain.append(orc.mag_fix(U.copy(), dims, 3, 1.7, 1e-12, 20000, 10, 50)["F"])
+        W = U.copy()
+        orc.mag_anneal(W, dims, 3, 0.6, 0.01, 300, 3, 60 + c, reunit_every=50)
+        ann.append(orc.mag_fix(W, dims, 3, 1.7, 1e-12, 20000, 10, 50)["F"])
+    assert np.mean(ann) > np.mean(plain)
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_mag_heatbath_draws_depend_on_the_sweep_word(orc, nc):
+    dims = (2, 4, 2, 4)
+    U = synth.gauge_config(dims, nc, 0.3, 13)
+    a, b, c = U.copy(), U.copy(), U.copy()
+    orc.mag_heatbath_sweep(a, dims, nc, 0.7, 21, 3)
+    orc.mag_heatbath_sweep(b, dims, nc, 0.7, 21, 4)
+    orc.mag_heatbath_sweep(c, dims, nc, 0.7, 21, 3)
+    assert np.abs(a - b).max() > 1e-3 and np.array_equal(a, c)
