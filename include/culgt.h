@@ -285,7 +285,12 @@ culgt_status culgt_validate_anneal(const culgt_anneal_params *a);
 
 /* One heat-bath sweep (black, then white) of a loaded handle at temperature
  * T > 0, drawing with the given seed and sweep word. In the FP32 phase of a
- * mixed handle it also accumulates g(x), like an overrelaxation sweep. */
+ * mixed handle it also accumulates g(x), like an overrelaxation sweep. For a
+ * CULGT_MAG handle each subgroup draws B = C Bmax (Bmax the MAG maximiser)
+ * with the block functional |z| (2u - 1), u = c0^2 + c3^2, from
+ * exp(functional / T): u by exact inversion, the two residual angles
+ * uniformly (counter (site, sweep, subgroup << 1, 0)); its microcanonical
+ * sweeps are MAG overrelaxation at omega = 2. */
 culgt_status culgt_handle_heatbath(culgt_handle *h, double T, unsigned long long seed, unsigned sweep_word);
 
 /* The heat-bath mapping the handle uses: whether the eight links stay in
@@ -294,6 +299,7 @@ culgt_status culgt_handle_heatbath(culgt_handle *h, double T, unsigned long long
  * scratch copy at the first heat-bath sweep for lattices of 65536 sites and
  * more, cached per storage and volume); every mapping gives the same links. */
 culgt_status culgt_handle_heatbath_tuning(culgt_handle *h, int *keep_links, int *min_blocks_per_sm);
+/* (CULGT_LANDAU handles; a MAG handle's heat bath has one mapping.) */
 
 /* The annealing schedule on a loaded handle: step k = 0 .. steps-1 is one
  * heat-bath sweep at T_k = t_start + (t_end - t_start) k / (steps - 1)
@@ -307,6 +313,11 @@ culgt_status culgt_handle_anneal(culgt_handle *h, const culgt_anneal_params *a);
  * between the load and the overrelaxation. */
 culgt_status culgt_landau_fix_anneal(void *d_links, const culgt_params *p, const culgt_anneal_params *a,
                                      void *cuda_stream, culgt_result *out);
+
+/* Maximally Abelian gauge fixing (culgt_mag_fix) with the annealing
+ * schedule run between the load and the overrelaxation. */
+culgt_status culgt_mag_fix_anneal(void *d_links, const culgt_params *p, const culgt_anneal_params *a,
+                                  void *cuda_stream, culgt_result *out);
 
 /* culgt_fix_batched with the annealing schedule run on every problem first
  * (in shared launches, all problems in step). Problem j draws with the key

@@ -450,19 +450,32 @@ culgt_status tuned_heatbath(culgt_handle *h, int *variant)
 
 culgt_status heatbath_now(culgt_handle *h, double T, unsigned long long seed, unsigned sweep)
 {
-    int v;
-    ST(tuned_heatbath(h, &v));
     const Ops *o = cur_ops(h);
     void *acc = (h->cur32 && h->gacc) ? h->gacc : nullptr;
+    if (h->prm.gauge == CULGT_MAG) {
+        for (int parity = 0; parity < 2; parity++)
+            o->mag_heatbath(cur_buf(h), acc, h->geom, parity, 1.0 / T, (uint32_t)seed, (uint32_t)(seed >> 32), sweep,
+                            h->stream);
+        return CULGT_OK;
+    }
+    int v;
+    ST(tuned_heatbath(h, &v));
     for (int parity = 0; parity < 2; parity++)
         o->heatbath(cur_buf(h), acc, h->geom, parity, 1.0 / T, (uint32_t)seed, (uint32_t)(seed >> 32), sweep, v,
                     h->stream);
     return CULGT_OK;
 }
 
-// overrelaxation at omega = 2 (r -> r^2 per subgroup keeps Re tr[r w])
+// overrelaxation at omega = 2 (r -> r^2 per subgroup keeps Re tr[r w]; for
+// MAG the smallest rotation applied twice keeps the block functional)
 culgt_status micro_now(culgt_handle *h)
 {
+    if (h->prm.gauge == CULGT_MAG) {
+        void *acc = (h->cur32 && h->gacc) ? h->gacc : nullptr;
+        for (int parity = 0; parity < 2; parity++)
+            cur_ops(h)->mag_halfsweep(cur_buf(h), acc, h->geom, parity, 2.0, 0, h->stream);
+        return CULGT_OK;
+    }
     Mapping m;
     ST(tuned_mapping(h, &m));
     const Ops *o = cur_ops(h);
@@ -881,7 +894,7 @@ culgt_status culgt_validate_anneal(const culgt_anneal_params *a) { return valida
 
 culgt_status culgt_handle_heatbath(culgt_handle *h, double T, unsigned long long seed, unsigned sweep_word)
 {
-    if (!h || !h->loaded || !(T > 0.0) || std::isinf(T) || h->prm.gauge != CULGT_LANDAU) return CULGT_ERR_ARG;
+    if (!h || !h->loaded || !(T > 0.0) || std::isinf(T)) return CULGT_ERR_ARG;
     CallScope scope(h);
     ST(heatbath_now(h, T, seed, sweep_word));
     CU(cudaGetLastError());
@@ -900,7 +913,7 @@ culgt_status culgt_handle_heatbath_tuning(culgt_handle *h, int *keep_links, int 
 
 culgt_status culgt_handle_anneal(culgt_handle *h, const culgt_anneal_params *a)
 {
-    if (!h || !h->loaded || h->prm.gauge != CULGT_LANDAU) return CULGT_ERR_ARG;
+    if (!h || !h->loaded) return CULGT_ERR_ARG;
     ST(validate_anneal(a));
     CallScope scope(h);
     return anneal_now(h, a);
@@ -915,6 +928,20 @@ culgt_status culgt_landau_fix_anneal(void *d_links, const culgt_params *p, const
     if (!d_links) return CULGT_ERR_ARG;
     HandleGuard g;
     ST(culgt_create(p, cuda_stream, &g.h));
+    return fix_call(g.h, d_links, d_links, out, t0, a);
+}
+
+culgt_status culgt_mag_fix_anneal(void *d_links, const culgt_params *p, const culgt_anneal_params *a,
+                                  void *cuda_stream, culgt_result *out)
+{
+    double t0 = now_seconds();
+    ST(validate(p));
+    ST(validate_anneal(a));
+    if (!d_links) return CULGT_ERR_ARG;
+    culgt_params q = *p;
+    q.gauge = CULGT_MAG;
+    HandleGuard g;
+    ST(culgt_create(&q, cuda_stream, &g.h));
     return fix_call(g.h, d_links, d_links, out, t0, a);
 }
 

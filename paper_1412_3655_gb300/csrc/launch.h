@@ -46,6 +46,9 @@ struct Ops {
     // 128); gacc as in halfsweep
     void (*mag_halfsweep)(void *base, void *gacc, const Geom &g, int parity, double omega, int variant,
                           cudaStream_t s);
+    // one MAG heat-bath half-sweep (simulated annealing), as heatbath
+    void (*mag_heatbath)(void *base, void *gacc, const Geom &g, int parity, double inv_temp, uint32_t k0, uint32_t k1,
+                         uint32_t sweep, cudaStream_t s);
     // per-block partial sums of (theta_MAG site terms, sum_mu sum_a |U_aa|^2); returns the block count
     int (*mag_theta_partials)(const void *base, const Geom &g, double2 *partials, cudaStream_t s);
     // per-block partial sums of (tr Delta Delta^+, sum Re tr U) over all sites; returns the block count

@@ -15,7 +15,7 @@
 // g exactly as in the Landau sweep.
 #pragma once
 
-#include "kernels.cuh"
+#include "anneal.cuh"
 
 namespace culgt {
 
@@ -82,25 +82,83 @@ template <typename T, int I, int J> __device__ __forceinline__ void rotate_cols_
     }
 }
 
-// The overrelaxed maximiser of one block: z from the (I, J) block of
-// X_I - X_J, the smallest rotation of z onto +e3, then r^omega. su2_or_step
-// takes a quaternion proportional to the conjugate of its maximiser.
-template <typename T, int I, int J>
-__device__ __forceinline__ void mag_block_step(const M3<T> X[3], T omega, int variant, T q[4])
+// conjugate of the MAG maximiser of a block with vector z (unnormalised):
+// the smallest rotation of z onto +e3 is the quaternion (|z| + z3, -z2, z1, 0);
+// z on (or by rounding past) -e3 takes i s1; z = 0 leaves the block alone
+template <typename T> __device__ __forceinline__ void mag_maximiser_conj(T z1, T z2, T z3, T n, T c[4])
+{
+    if (!(n > T(0))) {
+        c[0] = T(1), c[1] = c[2] = c[3] = T(0);
+    } else if (!(n + z3 > T(0))) {
+        c[0] = T(0), c[1] = T(-1), c[2] = c[3] = T(0);
+    } else {
+        c[0] = n + z3, c[1] = z2, c[2] = -z1, c[3] = T(0);
+    }
+}
+
+// The MAG subgroup steps: step(z1, z2, z3, s, q) turns the block vector z of
+// subgroup s into the SU(2) element q applied to the block.
+// Overrelaxation (Sec. 2) of the maximiser; su2_or_step takes a quaternion
+// proportional to the conjugate of its maximiser.
+template <typename T> struct MagOrStep {
+    T omega;
+    int variant;
+    __device__ __forceinline__ void operator()(T z1, T z2, T z3, int, T q[4]) const
+    {
+        const T n = sqrt(z1 * z1 + z2 * z2 + z3 * z3);
+        T c[4];
+        mag_maximiser_conj(z1, z2, z3, n, c);
+        su2_or_step(c[0], c[1], c[2], c[3], omega, variant, q);
+    }
+};
+
+// Heat bath (simulated annealing): B = C Bmax with the block functional
+// |z| (2u - 1), u = c0^2 + c3^2 uniform under Haar measure, so u is drawn
+// from exp(beta u) on [0, 1], beta = 2|z|/T, by inversion (w = 1 - u and u
+// each from its own logarithm while expm1(beta) is finite in range, beta <=
+// 30), and the two residual angles uniformly. Counter (site, sweep,
+// s << 1, 0): one Philox block per subgroup, no rejection.
+template <typename T> struct MagHbStep {
+    T beta_scale;  // 2 / T
+    uint32_t k0, k1, site, sweep;
+    __device__ __forceinline__ void operator()(T z1, T z2, T z3, int s, T q[4]) const
+    {
+        typedef typename DrawReal<T>::type S;
+        const T n = sqrt(z1 * z1 + z2 * z2 + z3 * z3);
+        if (!(n > T(0))) {
+            q[0] = T(1);
+            q[1] = q[2] = q[3] = T(0);
+            return;
+        }
+        T c[4];
+        mag_maximiser_conj(z1, z2, z3, n, c);
+        const T mn = rsqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2] + c[3] * c[3]);
+        const Q4<T> bmax = {{c[0] * mn, -c[1] * mn, -c[2] * mn, -c[3] * mn}};
+        const S beta = (S)(beta_scale * n);
+        const uint4 w = philox4x32_10(make_uint4(site, sweep, (uint32_t)s << 1, 0u), k0, k1);
+        const S v0 = unit_uniform<S>(w.x);
+        const S wv = -d_log1p(v0 * d_expm1(-beta)) / beta;
+        const S u = beta <= S(30) ? d_log1p((S(1) - v0) * d_expm1(beta)) / beta : S(1) - wv;
+        const S su = d_sqrt(u), sw = d_sqrt(wv);
+        S sa, ca, sc, cc;
+        d_sincospi(S(2) * unit_uniform<S>(w.y), &sa, &ca);
+        d_sincospi(S(2) * unit_uniform<S>(w.z), &sc, &cc);
+        const Q4<T> C = {{(T)(su * ca), (T)(sw * cc), (T)(sw * sc), (T)(su * sa)}};
+        Q4<T> r = q_mul(C, bmax);
+        const T m = rsqrt(r.a[0] * r.a[0] + r.a[1] * r.a[1] + r.a[2] * r.a[2] + r.a[3] * r.a[3]);
+#pragma unroll
+        for (int k = 0; k < 4; k++) q[k] = r.a[k] * m;
+    }
+};
+
+// one subgroup of the SU(3) MAG update: z from the (I, J) block of X_I - X_J
+template <typename T, int I, int J, class Step>
+__device__ __forceinline__ void mag_block_step(const M3<T> X[3], const Step &step, int s, T q[4])
 {
     const T z3 = T(0.5) * ((X[I].re[I][I] - X[J].re[I][I]) - (X[I].re[J][J] - X[J].re[J][J]));
     const T z1 = X[I].re[I][J] - X[J].re[I][J];
     const T z2 = -(X[I].im[I][J] - X[J].im[I][J]);
-    const T n = sqrt(z1 * z1 + z2 * z2 + z3 * z3);
-    T c0, c1, c2, c3;  // conjugate of the maximiser (unnormalised)
-    if (!(n > T(0))) {
-        c0 = T(1), c1 = c2 = c3 = T(0);
-    } else if (!(n + z3 > T(0))) {  // z on (or by rounding past) -e3
-        c0 = T(0), c1 = T(-1), c2 = c3 = T(0);  // maximiser i s1
-    } else {
-        c0 = n + z3, c1 = z2, c2 = -z1, c3 = T(0);  // maximiser (n + z3, -z2, z1, 0)
-    }
-    su2_or_step(c0, c1, c2, c3, omega, variant, q);
+    step(z1, z2, z3, s, q);
 }
 
 // X_a <- R X_a R^+ for the three X_a
@@ -114,17 +172,17 @@ template <typename T, int I, int J> __device__ __forceinline__ void mag_rotate_a
 }
 
 // SU(3) MAG site transformation g = R12 R02 R01 from the gathered X (consumed)
-template <typename T> __device__ __forceinline__ void mag_su3_gauge(M3<T> X[3], M3<T> &g, T omega, int variant)
+template <typename T, class Step> __device__ __forceinline__ void mag_su3_gauge(M3<T> X[3], M3<T> &g, const Step &step)
 {
     T q[4];
     m3_identity(g);
-    mag_block_step<T, 0, 1>(X, omega, variant, q);
+    mag_block_step<T, 0, 1>(X, step, 0, q);
     rotate_rows<T, 0, 1>(g, q);
     mag_rotate_all<T, 0, 1>(X, q);
-    mag_block_step<T, 0, 2>(X, omega, variant, q);
+    mag_block_step<T, 0, 2>(X, step, 1, q);
     rotate_rows<T, 0, 2>(g, q);
     mag_rotate_all<T, 0, 2>(X, q);
-    mag_block_step<T, 1, 2>(X, omega, variant, q);
+    mag_block_step<T, 1, 2>(X, step, 2, q);
     rotate_rows<T, 1, 2>(g, q);
 }
 
@@ -190,17 +248,18 @@ __device__ __forceinline__ void mag_gather_su2(const typename P::Chunk *base, co
     }
 }
 
-// One MAG half-sweep site update (1 thread per site); gout receives g.
-template <class P>
+// One MAG half-sweep site update (1 thread per site) with the given block
+// step; gout receives g.
+template <class P, class Step>
 __device__ __forceinline__ void mag_site_update(typename P::Chunk *base, const Geom &g, int cb, int p,
-                                                typename P::Real omega, int variant, M3<typename P::Real> *gout)
+                                                const Step &step, M3<typename P::Real> *gout)
 {
     typedef typename P::Real T;
     int x[4];
     decode_site(g, cb, p, x);
     M3<T> X[3], G;
     mag_gather<P>(base, g, cb, p, x, X);
-    mag_su3_gauge(X, G, omega, variant);
+    mag_su3_gauge(X, G, step);
 #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
         typename P::Chunk *fp = base + plane_offset(g, p, mu, P::NCHUNK) + cb;
@@ -216,26 +275,17 @@ __device__ __forceinline__ void mag_site_update(typename P::Chunk *base, const G
     *gout = G;
 }
 
-template <class P>
+template <class P, class Step>
 __device__ __forceinline__ void mag_site_update(typename P::Chunk *base, const Geom &g, int cb, int p,
-                                                typename P::Real omega, int variant, Q4<typename P::Real> *gout)
+                                                const Step &step, Q4<typename P::Real> *gout)
 {
     typedef typename P::Real T;
     int x[4];
     decode_site(g, cb, p, x);
     T z[3];
     mag_gather_su2<P>(base, g, cb, p, x, z);
-    const T n = sqrt(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]);
-    T c0, c1, c2, c3;
-    if (!(n > T(0))) {
-        c0 = T(1), c1 = c2 = c3 = T(0);
-    } else if (!(n + z[2] > T(0))) {
-        c0 = T(0), c1 = T(-1), c2 = c3 = T(0);
-    } else {
-        c0 = n + z[2], c1 = z[1], c2 = -z[0], c3 = T(0);
-    }
     Q4<T> G;
-    su2_or_step(c0, c1, c2, c3, omega, variant, G.a);
+    step(z[0], z[1], z[2], 0, G.a);
 #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
         typename P::Chunk *fp = base + plane_offset(g, p, mu, P::NCHUNK) + cb;
@@ -257,7 +307,23 @@ __global__ void __launch_bounds__(128) k_mag_halfsweep(typename P::Chunk *base, 
     const int cb = blockIdx.x * blockDim.x + threadIdx.x;
     if (cb >= g.Vh) return;
     typename P::Link G;
-    mag_site_update<P>(base, g, cb, parity, omega, variant, &G);
+    mag_site_update<P>(base, g, cb, parity, MagOrStep<typename P::Real>{omega, variant}, &G);
+    if (acc) accumulate_gauge<P, PG>(gacc, g, parity, cb, G);
+}
+
+// MAG heat-bath half-sweep at 1/T = inv_temp (simulated annealing), draws
+// keyed by (k0, k1) with the canonical site index and sweep word
+template <class P, class PG>
+__global__ void __launch_bounds__(128) k_mag_heatbath(typename P::Chunk *base, typename PG::Chunk *gacc, Geom g,
+                                                      int parity, double inv_temp, uint32_t k0, uint32_t k1,
+                                                      uint32_t sweep, int acc)
+{
+    typedef typename P::Real T;
+    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cb >= g.Vh) return;
+    const MagHbStep<T> step{(T)(2.0 * inv_temp), k0, k1, canonical_site(g, cb, parity), sweep};
+    typename P::Link G;
+    mag_site_update<P>(base, g, cb, parity, step, &G);
     if (acc) accumulate_gauge<P, PG>(gacc, g, parity, cb, G);
 }
 

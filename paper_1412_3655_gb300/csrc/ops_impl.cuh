@@ -87,6 +87,14 @@ template <class P> struct OpsImpl {
             (C *)base, (typename PG::Chunk *)gacc, g, parity, (typename P::Real)omega, variant, gacc != nullptr);
         count_launch();
     }
+    static void mag_heatbath(void *base, void *gacc, const Geom &g, int parity, double inv_temp, uint32_t k0,
+                             uint32_t k1, uint32_t sweep, cudaStream_t s)
+    {
+        typedef typename GaugeParam<P>::type PG;
+        k_mag_heatbath<P, PG><<<blocks_for(g.Vh, 128), 128, 0, s>>>((C *)base, (typename PG::Chunk *)gacc, g, parity,
+                                                                     inv_temp, k0, k1, sweep, gacc != nullptr);
+        count_launch();
+    }
     static int mag_theta_partials(const void *base, const Geom &g, double2 *partials, cudaStream_t s)
     {
         unsigned nb = blocks_for(2LL * g.Vh, kThetaThreads);
@@ -168,6 +176,7 @@ template <class P> struct OpsImpl {
         o.theta_partials = theta_partials;
         o.mag_halfsweep = mag_halfsweep;
         o.mag_theta_partials = mag_theta_partials;
+        o.mag_heatbath = mag_heatbath;
         o.plaq_partials = plaq_partials;
         o.reunitarize = reunitarize;
         o.gauge_identity = kFP32 ? gauge_identity : nullptr;

@@ -196,6 +196,7 @@ def library():
         "culgt_landau_fix_anneal": (ip, [vp, P, A, vp, R]),
         "culgt_fix_batched_anneal": (ip, [ctypes.POINTER(_Problem), ip, P, A, vp, R]),
         "culgt_coulomb_fix_anneal": (ip, [vp, P, A, vp, R, vp]),
+        "culgt_mag_fix_anneal": (ip, [vp, P, A, vp, R]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -351,6 +352,15 @@ def culgt_landau_fix_anneal(links, params: Params, anneal: AnnealParams, stream=
     st = _check(library().culgt_landau_fix_anneal(_links_ptr(links, params, True), ctypes.byref(params._c()),
                                                   ctypes.byref(anneal._c()), _stream(stream), ctypes.byref(r)),
                 "culgt_landau_fix_anneal")
+    return Result._from(r, st)
+
+
+def culgt_mag_fix_anneal(links, params: Params, anneal: AnnealParams, stream=None) -> Result:
+    """Simulated annealing with MAG heat-bath sweeps, then MAG fixing, in place."""
+    r = _Result()
+    st = _check(library().culgt_mag_fix_anneal(_links_ptr(links, params, True), ctypes.byref(params._c()),
+                                               ctypes.byref(anneal._c()), _stream(stream), ctypes.byref(r)),
+                "culgt_mag_fix_anneal")
     return Result._from(r, st)
 
 

@@ -185,3 +185,68 @@ def test_full_size_mag_sweep(cu, orc, nc):
     d = to_dev(U)
     cu.culgt_sweep(d, cu.Params.defaults(nc, dims, gauge=cu.MAG), 1)
     assert_close(from_dev(d, U.shape), ref, 1e-13, False)
+
+
+SEED = 0x0DDC0FFEE
+
+
+def mag_heatbath_on_device(cu, U, dims, nc, T, word, **kw):
+    d = to_dev(U)
+    p = cu.Params.defaults(nc, dims, gauge=cu.MAG, **kw)
+    with cu.Handle(p) as h:
+        h.culgt_load(d)
+        h.culgt_handle_heatbath(T, SEED, word)
+        h.culgt_store(d)
+    torch.cuda.synchronize()
+    return from_dev(d, U.shape)
+
+
+@pytest.mark.parametrize("dims,nc", CASES)
+@pytest.mark.parametrize("T", [0.05, 2.0])
+def test_one_mag_heatbath_sweep_fp64(cu, orc, dims, nc, T):
+    U0 = synth.gauge_config(dims, nc, 0.3, 2)
+    for U, good in [(U0, False), (mag_warmed(U0, dims, nc, orc), True)]:
+        ref = U.copy()
+        orc.mag_heatbath_sweep(ref, dims, nc, T, SEED, 5)
+        for sr in ([18, 12] if nc == 3 else [4]):
+            assert_close(mag_heatbath_on_device(cu, U, dims, nc, T, 5, storage_reals=sr), ref, 1e-13, good)
+
+
+@pytest.mark.parametrize("dims,nc", CASES)
+def test_one_mag_heatbath_sweep_fp32(cu, orc, dims, nc):
+    U = round32(mag_warmed(synth.gauge_config(dims, nc, 0.3, 3), dims, nc, orc))
+    ref = U.copy()
+    orc.mag_heatbath_sweep(ref, dims, nc, 0.5, SEED, 2)
+    got = mag_heatbath_on_device(cu, U, dims, nc, 0.5, 2, precision=cu.FP32)
+    assert_close(got, ref, 5e-6, False, q=0.99)
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_mag_fix_anneal_fp64_matches_oracle(cu, orc, nc):
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_config(dims, nc, 0.5, 1)
+    ref = U.copy()
+    orc.mag_anneal(ref, dims, nc, 0.6, 0.05, 20, 2, SEED, reunit_every=50)
+    rr = orc.mag_fix(ref, dims, nc, 1.7, 1e-12, 5000, 5, 50)
+    d = to_dev(U)
+    p = cu.Params.defaults(nc, dims, check_every=5, reunit_every=50, max_sweeps=5000)
+    r = cu.culgt_mag_fix_anneal(d, p, cu.AnnealParams(0.6, 0.05, 20, 2, SEED))
+    assert r.status == cu.OK and r.theta < 1e-12
+    assert r.sweeps_fp64 == rr["sweeps"]
+    assert r.F == pytest.approx(rr["F"], rel=1e-10)
+    assert r.plaq_after == pytest.approx(r.plaq_before, abs=1e-12)
+    assert np.abs(np.abs(from_dev(d, U.shape)) - np.abs(ref)).max() < 1e-9
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_mag_fix_anneal_mixed(cu, orc, nc):
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_config(dims, nc, 0.5, 1)
+    d = to_dev(U)
+    p = cu.Params.defaults(nc, dims, precision=cu.MIXED, check_every=5, reunit_every=50, max_sweeps=5000)
+    r = cu.culgt_mag_fix_anneal(d, p, cu.AnnealParams(0.6, 0.05, 20, 2, SEED))
+    assert r.status == cu.OK and r.theta < 1e-12 and r.sweeps_fp32 > 0
+    out = from_dev(d, U.shape)
+    th, F = orc.mag_theta(out, dims, nc)
+    assert th < 1e-12 and F == pytest.approx(r.F, rel=1e-12)
+    assert orc.plaquette(out, dims, nc) == pytest.approx(orc.plaquette(U, dims, nc), abs=1e-12)
