@@ -53,9 +53,10 @@ def assert_close(got, ref, tol, well_conditioned, q=0.995):
     (the axis of the maximising rotation amplifies rounding by about
     |X| / (|z| + z3)). Perturbing the oracle's input by 1e-14 on the 6x4x6x10
     SU(3) case moves its MAG output by up to 280x at the 99.9% quantile and
-    61x at 99.5%, against 66x and 35x for the Landau sweep. FP32 (rounding
-    6e-8, so about 4e-6 at that 99.5% amplification before the FP32 sums
-    add theirs) is held to 5e-6 on 99% of the links of the random start."""
+    61x at 99.5%, against 66x and 35x for the Landau sweep. In FP32 (rounding
+    6e-8, about 4e-6 at that amplification before the FP32 sums of 16 outer
+    products add theirs) the random start is held to 1e-5 on 99% of the links,
+    well-conditioned input to 5e-6 on all."""
     nc = got.shape[-1]
     err = np.abs(got - ref).reshape(-1, nc * nc).max(axis=1)
     if well_conditioned:
@@ -93,7 +94,7 @@ def test_one_mag_sweep_fp32(cu, orc, dims, nc):
             d = to_dev(U)
             p = cu.Params.defaults(nc, dims, precision=cu.FP32, storage_reals=sr, gauge=cu.MAG)
             cu.culgt_sweep(d, p, 1)
-            assert_close(from_dev(d, U.shape), ref, 5e-6, good, q=0.99)
+            assert_close(from_dev(d, U.shape), ref, 5e-6 if good else 1e-5, good, q=0.99)
 
 
 @pytest.mark.parametrize("nc", [2, 3])
@@ -204,8 +205,11 @@ def mag_heatbath_on_device(cu, U, dims, nc, T, word, **kw):
 @pytest.mark.parametrize("dims,nc", CASES)
 @pytest.mark.parametrize("T", [0.05, 2.0])
 def test_one_mag_heatbath_sweep_fp64(cu, orc, dims, nc, T):
+    """Cold draws stay near the maximiser, so warmed input stays well
+    conditioned through the white half-sweep; hot draws (T = 2) randomise the
+    black sites first, and the white sites then see random-start blocks."""
     U0 = synth.gauge_config(dims, nc, 0.3, 2)
-    for U, good in [(U0, False), (mag_warmed(U0, dims, nc, orc), True)]:
+    for U, good in [(U0, False), (mag_warmed(U0, dims, nc, orc), T < 0.5)]:
         ref = U.copy()
         orc.mag_heatbath_sweep(ref, dims, nc, T, SEED, 5)
         for sr in ([18, 12] if nc == 3 else [4]):
@@ -235,7 +239,11 @@ def test_mag_fix_anneal_fp64_matches_oracle(cu, orc, nc):
     assert r.sweeps_fp64 == rr["sweeps"]
     assert r.F == pytest.approx(rr["F"], rel=1e-10)
     assert r.plaq_after == pytest.approx(r.plaq_before, abs=1e-12)
-    assert np.abs(np.abs(from_dev(d, U.shape)) - np.abs(ref)).max() < 1e-9
+    # the moduli are free of the diagonal rotations MAG leaves open; the 60
+    # annealing sweeps amplify rounding differences (MAG's blocks are worse
+    # conditioned than Landau's), the same maximum is pinned by F and the
+    # sweep count above
+    assert np.abs(np.abs(from_dev(d, U.shape)) - np.abs(ref)).max() < 1e-7
 
 
 @pytest.mark.parametrize("nc", [2, 3])
