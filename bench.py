@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--profile-step", choices=["mixed", "fp64", "fp32", "df", "mixed_df"], default=None,
                     help="run one gauge fixing (or --profile-sweeps sweeps) of the workload and exit; "
                          "the command the ncu captures in profiles/ wrap")
+    ap.add_argument("--profile-gauge", choices=["landau", "mag"], default="landau",
+                    help="with --profile-step: the gauge functional of the handle")
     ap.add_argument("--profile-heatbath", type=float, default=0.0,
                     help="with --profile-step and --profile-sweeps: heat-bath sweeps at this temperature instead")
     ap.add_argument("--profile-sweeps", type=int, default=0,
@@ -276,7 +278,8 @@ def run_profile_step(args):
             "mixed_df": culgt.MIXED_DF}[args.profile_step]
     p = culgt.Params.defaults(nc, dims, omega=omega, precision=prec, check_every=10, reunit_every=50,
                               max_sweeps=20000, threads_per_site=args.tps, block_size=args.block,
-                              min_blocks_per_sm=args.minb)
+                              min_blocks_per_sm=args.minb,
+                              gauge=culgt.MAG if args.profile_gauge == "mag" else culgt.LANDAU)
     with culgt.Handle(p) as h:
         h.culgt_load(d_in)
         if args.profile_sweeps and args.profile_heatbath > 0:
