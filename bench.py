@@ -120,7 +120,7 @@ def measured_peaks():
 
 # files that define the single-lattice sweep kernels: a recorded ncu traffic
 # figure holds only while these are unchanged
-KERNEL_SOURCES = ("culgt_device.cuh", "dfloat.cuh", "kernels.cuh", "ops_impl.cuh", "anneal.cuh")
+KERNEL_SOURCES = ("culgt_device.cuh", "dfloat.cuh", "kernels.cuh", "ops_impl.cuh", "anneal.cuh", "mag.cuh")
 
 
 def source_hash():
@@ -332,7 +332,8 @@ def run_mag(args):
             ms = a.elapsed_time(b) / (2 * n)
             gbs = (V // 2) * bps / (ms / 1e3) / 1e9
             kernels[name] = {"launch_ms": ms, "algorithmic_GB_per_s": gbs, "hbm_frac": gbs / hbm,
-                             "peak_source": f"{src} hbm_gbs"}
+                             "peak_source": f"{src} hbm_gbs",
+                             "traffic": recorded_traffic(f"mag_halfsweep_su3_{name[:3]}_{name[4:]}_b128")}
     fixes = {}
     for name, prec in [("mixed", culgt.MIXED), ("fp64", culgt.FP64)]:
         p = culgt.Params.defaults(nc, dims, omega=omega, precision=prec, check_every=10, reunit_every=50,
