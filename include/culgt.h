@@ -27,6 +27,13 @@
  *             theta_t, F_t normalised by V3 = L1 L2 L3 and its own
  *             checkerboard (black = x1 + x2 + x3 even).
  *
+ * Beyond the Landau/Coulomb overrelaxation of Sec. 2 the library fixes the
+ * maximally Abelian gauge (culgt_gauge, culgt_mag_fix) with the same
+ * checkerboard skeleton, and combines either gauge with simulated annealing
+ * (culgt_anneal_params and the *_anneal entry points): the two other parts of
+ * the paper's cuLGT that it names without formulas; the readings are stated
+ * beside those declarations.
+ *
  * Errors: every function returns a culgt_status and throws nothing. Arguments
  * are validated before any device work. A CUDA error maps to CULGT_ERR_CUDA;
  * the library never prints. Work is ordered on the caller's stream (NULL =
