@@ -237,6 +237,31 @@ bool mapping_allowed(const culgt_params &p, const Mapping &m)
     return true;
 }
 
+// scratch copy and timing events of a tuner, released on every return path
+struct TuneScratch {
+    void *p = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    culgt_status init(size_t bytes)
+    {
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            (void)cudaGetLastError();
+            p = nullptr;
+            return CULGT_ERR_OOM;
+        }
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return CULGT_ERR_CUDA;
+        }
+        return CULGT_OK;
+    }
+    ~TuneScratch()
+    {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (p) cudaFree(p);
+    }
+};
+
 culgt_status autotune(culgt_handle *h, const Ops *o, void *buf, bool acc, Mapping *out)
 {
     const culgt_params &p = h->prm;
@@ -264,15 +289,10 @@ culgt_status autotune(culgt_handle *h, const Ops *o, void *buf, bool acc, Mappin
     }
     size_t bytes = buffer_bytes(o, h->geom);
     size_t gbytes = acc ? gauge_bytes(o, h->geom) : 0;
-    void *scratch = nullptr, *gscratch = nullptr;
-    if (cudaMalloc(&scratch, bytes + gbytes) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return CULGT_ERR_OOM;
-    }
-    if (acc) gscratch = (char *)scratch + bytes;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    TuneScratch ts;
+    ST(ts.init(bytes + gbytes));
+    void *scratch = ts.p, *gscratch = acc ? (char *)ts.p + bytes : nullptr;
+    cudaEvent_t e0 = ts.e0, e1 = ts.e1;
     CU(cudaMemcpyAsync(scratch, buf, bytes, cudaMemcpyDeviceToDevice, h->stream));
     if (acc) CU(cudaMemcpyAsync(gscratch, h->gacc, gbytes, cudaMemcpyDeviceToDevice, h->stream));
     float times[sizeof(kMappings) / sizeof(kMappings[0])];
@@ -303,9 +323,6 @@ culgt_status autotune(culgt_handle *h, const Ops *o, void *buf, bool acc, Mappin
             pick = kMappings[k];
             break;
         }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaFree(scratch);
     CU(cudaGetLastError());
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -404,17 +421,12 @@ culgt_status tuned_heatbath(culgt_handle *h, int *variant)
         if (!cached) {
             size_t bytes = buffer_bytes(o, h->geom);
             size_t gbytes = acc ? gauge_bytes(o, h->geom) : 0;
-            void *scratch = nullptr;
-            if (cudaMalloc(&scratch, bytes + gbytes) != cudaSuccess) {
-                (void)cudaGetLastError();
-                return CULGT_ERR_OOM;
-            }
-            void *gscratch = acc ? (char *)scratch + bytes : nullptr;
+            TuneScratch ts;
+            ST(ts.init(bytes + gbytes));
+            void *scratch = ts.p, *gscratch = acc ? (char *)ts.p + bytes : nullptr;
+            cudaEvent_t e0 = ts.e0, e1 = ts.e1;
             CU(cudaMemcpyAsync(scratch, cur_buf(h), bytes, cudaMemcpyDeviceToDevice, h->stream));
             if (acc) CU(cudaMemcpyAsync(gscratch, h->gacc, gbytes, cudaMemcpyDeviceToDevice, h->stream));
-            cudaEvent_t e0, e1;
-            cudaEventCreate(&e0);
-            cudaEventCreate(&e1);
             float best = 1e30f, times[8];
             const int nv = o->heatbath_variants < 8 ? o->heatbath_variants : 8;
             for (int v = 0; v < nv; v++) {
@@ -435,9 +447,6 @@ culgt_status tuned_heatbath(culgt_handle *h, int *variant)
                     pick = v;
                     break;
                 }
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            cudaFree(scratch);
             CU(cudaGetLastError());
             std::lock_guard<std::mutex> lock(g_tune_mutex);
             g_hb_cache[key] = pick;
