@@ -615,11 +615,11 @@ def run_culgt(args):
     # per-kernel launch times: back-to-back half-sweeps on the launching stream
     mapping = {}
 
-    def kernel_ms(params, n_sweeps=100):
+    def kernel_ms(params, n_sweeps=100, links=None, prefix=""):
         with culgt.Handle(params, stream) as hk:
-            hk.culgt_load(d_in)
+            hk.culgt_load(d_in if links is None else links)
             hk.culgt_handle_sweep(5)
-            mapping[{culgt.MIXED: "fp32_phase", culgt.FP64: "fp64", culgt.DF: "double_float"}.get(
+            mapping[prefix + {culgt.MIXED: "fp32_phase", culgt.FP64: "fp64", culgt.DF: "double_float"}.get(
                 params.precision, str(params.precision))] = hk.culgt_handle_tuning()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -639,18 +639,18 @@ def run_culgt(args):
     def roofline_hbm(key, t_ms, m):
         bytes_launch = (V // 2) * BYTES_PER_SITE[key]
         achieved = bytes_launch / (t_ms / 1e3) / 1e9
-        name = (f"halfsweep_su{nc}_{'f32' if key[1] else 'f64'}_{key[2]}" + ("_acc" if len(key) > 3 else "")
+        name = (f"halfsweep_su{key[0]}_{'f32' if key[1] else 'f64'}_{key[2]}" + ("_acc" if len(key) > 3 else "")
                 + f"_tps{m[0]}_b{m[1]}_mb{m[2]}")
         return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": recorded_traffic(name), "kernel": name, "launch_ms": t_ms,
                 "algorithmic_bytes_per_launch": bytes_launch, "peak_source": f"{peak_src} hbm_gbs"}
 
     def roofline_fp64(key, t_ms, m):
-        # FP64-ALU bound on GB300: algorithmic FP64 flops per SU(3) site update
+        # FP64-ALU bound on GB300: algorithmic FP64 flops per site update
         # (FMA = 2) against 2 DFMA/clock/SM x 152 SMs x 2070 MHz
-        flops_launch = (V // 2) * FLOPS_PER_SITE[nc]
+        flops_launch = (V // 2) * FLOPS_PER_SITE[key[0]]
         achieved = flops_launch / (t_ms / 1e3) / 1e12
-        name = f"halfsweep_su{nc}_{'f32' if key[1] else 'f64'}_{key[2]}_tps{m[0]}_b{m[1]}_mb{m[2]}"
+        name = f"halfsweep_su{key[0]}_{'f32' if key[1] else 'f64'}_{key[2]}_tps{m[0]}_b{m[1]}_mb{m[2]}"
         return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(name), "kernel": name,
                 "launch_ms": t_ms, "algorithmic_flops_per_launch": flops_launch,
@@ -682,17 +682,19 @@ def run_culgt(args):
 
     # time to theta < 1e-12 on the same input: plain FP64, and the double-float
     # variants (FP64-size links as float pairs, FP32-pipe arithmetic, theta in FP64)
-    def fix_time(params):
+    def fix_time(params, links=None):
         hx = culgt.Handle(params, stream)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        hx.culgt_load(d_in)
+        hx.culgt_load(d_in if links is None else links)
         r = hx.culgt_handle_fix()
-        hx.culgt_store(d_out)
+        hx.culgt_store(d_out if links is None else links_out[0])
         b.record(stream)
         torch.cuda.synchronize()
         hx.close()
         return a.elapsed_time(b) / 1e3, r
+
+    links_out = [None]
 
     fp64_s, rp = fix_time(plain)
     mixed_df = culgt.Params(**{**mixed.__dict__, "precision": culgt.MIXED_DF})
@@ -718,6 +720,27 @@ def run_culgt(args):
     for sw in (1e-10, 1e-11):
         t_sw, r_sw = fix_time(culgt.Params(**{**mixed.__dict__, "switch_theta": sw}))
         late[f"{sw:g}"] = {"s": t_sw, "sweeps": [r_sw.sweeps_fp32, r_sw.sweeps_fp64], "F": r_sw.F, "theta": r_sw.theta}
+
+    # SU(2) on the same generator (eps 0.3, Haar g, seed 2) and lattice: the
+    # per-phase half-sweep rates and the time to theta < 1e-12, mixed vs FP64
+    U2 = synth.gauge_config(dims, 2, eps, seed)
+    d2 = torch.from_numpy(U2.view(np.float64).copy()).to(dev)
+    del U2
+    links_out[0] = torch.empty_like(d2)
+    mixed2 = culgt.Params(**{**mixed.__dict__, "nc": 2})
+    plain2 = culgt.Params(**{**plain.__dict__, "nc": 2})
+    t2_32 = kernel_ms(mixed2, 100, d2, "su2_")
+    t2_64 = kernel_ms(plain2, 50, d2, "su2_")
+    su2_mixed_s, r2m = fix_time(mixed2, d2)
+    su2_fp64_s, r2p = fix_time(plain2, d2)
+    su2 = {
+        "fp32_phase": roofline_hbm((2, 1, 4, "acc"), t2_32, mapping["su2_fp32_phase"]),
+        "fp64": roofline_fp64((2, 0, 4), t2_64, mapping["su2_fp64"]),
+        "time_to_theta": {"mixed_s": su2_mixed_s, "mixed_sweeps": [r2m.sweeps_fp32, r2m.sweeps_fp64],
+                          "mixed_F": r2m.F, "fp64_s": su2_fp64_s, "fp64_sweeps": r2p.sweeps_fp64, "fp64_F": r2p.F},
+    }
+    del d2
+    links_out[0] = None
 
     # end to end through the host entry point (pinned host buffer)
     pinned = host.pin_memory()
@@ -753,6 +776,7 @@ def run_culgt(args):
         "roofline": dominant,
         "roofline_kernels": {"fp32_phase": rl32, "fp64": rl64, "double_float": rldf,
                              "heatbath_fp32_phase": rlhb32, "heatbath_fp64": rlhb64},
+        "su2": su2,
         "gpu_launches": launches,
         "sweep_mapping": {k: ({"keep_links": v[0], "block": v[1], "min_blocks_per_sm": v[2]} if
                               k.startswith("heatbath") else
