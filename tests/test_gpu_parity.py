@@ -345,6 +345,28 @@ def test_full_size_32_one_sweep(cu, orc, nc):
         del d
 
 
+def test_full_size_64_one_sweep(cu, orc):
+    """64^4 SU(3) (16.8M sites, eps 0.25, seed 3, omega 1.75: the largest
+    lattice of the measurements), the whole lattice in the mapping the
+    autotuner picks for it: one FP64 18-real sweep and one FP32 12-real sweep
+    against the oracle, from the random Haar start (99.9% of links within
+    tolerance, all within 1000 x)."""
+    dims = (64, 64, 64, 64)
+    U = synth.gauge_config(dims, 3, 0.25, 3)
+    ref = U.copy()
+    orc.sweep(ref, dims, 3, 1.75, 1)
+    d = to_dev(U)
+    cu.culgt_sweep(d, cu.Params.defaults(3, dims, omega=1.75), 1)
+    assert_sweep_close(from_dev(d, U.shape), ref, 1e-13, False)
+    del d, ref
+    U = round32(U)
+    ref = U.copy()
+    orc.sweep(ref, dims, 3, 1.75, 1)
+    d = to_dev(U)
+    cu.culgt_sweep(d, cu.Params.defaults(3, dims, omega=1.75, precision=cu.FP32), 1)
+    assert_sweep_close(from_dev(d, U.shape), ref, 5e-6, False)
+
+
 @pytest.mark.parametrize("nc,precision,storage", [(3, 0, 18), (3, 0, 12), (3, 1, 12), (3, 1, 18), (3, 4, 0),
                                                   (2, 0, 4), (2, 1, 4), (2, 4, 0), (3, 2, 12), (2, 2, 4)])
 def test_every_mapping_gives_identical_links(cu, nc, precision, storage):
