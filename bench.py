@@ -737,10 +737,11 @@ def run_culgt(args):
     # FP32 quaternion links (4V x 16 B) and the g accumulator (V x 16 B) fit in
     # L2 at 32^4: that half-sweep runs from L2, so no HBM fraction is claimed
     rl2_32 = roofline_hbm((2, 1, 4, "acc"), t2_32, mapping["su2_fp32_phase"])
-    ws = 5 * V * 16
-    if ws < L2_BYTES:
-        rl2_32.update({"bound": "l2-resident", "frac": None, "working_set_bytes": ws,
-                       "note": f"working set {ws / 1e6:.0f} MB < L2 {L2_BYTES / 1e6:.0f} MB: achieved is an L2 rate"})
+    su2_bytes = 5 * V * 16
+    if su2_bytes < L2_BYTES:
+        rl2_32.update({"bound": "l2-resident", "frac": None, "working_set_bytes": su2_bytes,
+                       "note": f"working set {su2_bytes / 1e6:.0f} MB < L2 {L2_BYTES / 1e6:.0f} MB: "
+                               "achieved is an L2 rate"})
     su2 = {
         "fp32_phase": rl2_32,
         "fp64": roofline_fp64((2, 0, 4), t2_64, mapping["su2_fp64"]),
