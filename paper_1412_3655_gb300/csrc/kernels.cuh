@@ -110,19 +110,39 @@ __device__ __forceinline__ void su3_update(typename P::Chunk *base, const Geom &
     }
     M3<T> G;
     su3_local_gauge_step(K, G, step);
+    if constexpr (!KEEP && std::is_same<T, dfl>::value) {
+        // double-float: one copy of the update code for all directions (the
+        // unrolled float-float arithmetic otherwise overflows the instruction
+        // cache); same arithmetic, so the links are the same
+#pragma unroll 1
+        for (int k = 0; k < NMU; k++) {
+            const int mu = mu0 + k;
+            if (mu < mu_first || !valid) continue;
+            C *fp = base + plane_offset(g, p, mu, P::NCHUNK) + cb;
+            C *bp = base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1);
+            M3<T> u, t;
+            P::load(fp, g.stride, u);
+            apply_left<P>(t, G, u);
+            P::store(fp, g.stride, t);
+            P::load(bp, g.stride, u);
+            apply_right_adj<P>(t, u, G);
+            P::store(bp, g.stride, t);
+        }
+    } else {
 #pragma unroll
-    for (int k = 0; k < NMU; k++) {
-        const int mu = mu0 + k;
-        if (mu < mu_first || !valid) continue;
-        M3<T> &f = uf[KEEP ? k : 0];
-        M3<T> &b = ub[KEEP ? k : 0];
-        M3<T> t;
-        if (!KEEP) P::load(fwd[k], g.stride, f);
-        apply_left<P>(t, G, f);
-        P::store(fwd[k], g.stride, t);
-        if (!KEEP) P::load(bwd[k], g.stride, b);
-        apply_right_adj<P>(t, b, G);
-        P::store(bwd[k], g.stride, t);
+        for (int k = 0; k < NMU; k++) {
+            const int mu = mu0 + k;
+            if (mu < mu_first || !valid) continue;
+            M3<T> &f = uf[KEEP ? k : 0];
+            M3<T> &b = ub[KEEP ? k : 0];
+            M3<T> t;
+            if (!KEEP) P::load(fwd[k], g.stride, f);
+            apply_left<P>(t, G, f);
+            P::store(fwd[k], g.stride, t);
+            if (!KEEP) P::load(bwd[k], g.stride, b);
+            apply_right_adj<P>(t, b, G);
+            P::store(bwd[k], g.stride, t);
+        }
     }
     if (gout) *gout = G;
 }
