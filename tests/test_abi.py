@@ -170,3 +170,21 @@ def test_coulomb_anneal_rejects_before_device_work(lib):
                                        None, None) == lib.ERR_ARG
     assert so.culgt_coulomb_fix_anneal(ctypes.c_void_p(16), ctypes.byref(p._c()), None, None, None,
                                        None) == lib.ERR_ARG
+
+
+def test_batched_empty_and_bad_problems_rejected(lib):
+    """An empty batch, a NULL problem table or links pointer, and a problem
+    with odd dims are refused before any device work."""
+    so = lib.library()
+    p = lib.Params.defaults(3, (4, 4, 4, 4))
+    probs = (lib._Problem * 2)()
+    probs[0].d_links = 16
+    probs[0].dims = (ctypes.c_int * 4)(4, 4, 4, 4)
+    probs[1].d_links = 16
+    probs[1].dims = (ctypes.c_int * 4)(4, 3, 4, 4)
+    assert so.culgt_fix_batched(probs, 0, ctypes.byref(p._c()), None, None) == lib.ERR_ARG
+    assert so.culgt_fix_batched(None, 1, ctypes.byref(p._c()), None, None) == lib.ERR_ARG
+    assert so.culgt_fix_batched(probs, 2, ctypes.byref(p._c()), None, None) == lib.ERR_DIMS
+    probs[1].dims = (ctypes.c_int * 4)(4, 4, 4, 4)
+    probs[1].d_links = None
+    assert so.culgt_fix_batched(probs, 2, ctypes.byref(p._c()), None, None) == lib.ERR_ARG

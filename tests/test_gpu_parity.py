@@ -429,3 +429,27 @@ def test_checkpoint_and_resume(cu, nc):
     r2 = cu.culgt_landau_fix(part, rest)
     assert r2.sweeps_fp64 + 20 == rw.sweeps_fp64
     assert torch.equal(part, whole)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("nc", [2, 3])
+def test_degenerate_block_is_left_alone(cu, orc, nc, precision):
+    """det = 0 (reading 4): all links 1 except the four backward links of the
+    origin, -1 (SU(2)) or diag(-1, -1, 1) (SU(3)), so K(0) = 0 (SU(2)) or its
+    (0,1) block is 0 (SU(3)). One sweep matches the oracle, which leaves that
+    block alone."""
+    dims = (4, 4, 4, 4)
+    V = int(np.prod(dims))
+    U = np.broadcast_to(np.eye(nc, dtype=complex), (V, 4, nc, nc)).copy()
+    m = -np.eye(2, dtype=complex) if nc == 2 else np.diag([-1.0 + 0j, -1.0, 1.0])
+    for mu in range(4):
+        ib = int(np.flatnonzero(synth.site_neighbour_forward(dims, mu) == 0)[0])
+        U[ib, mu] = m
+    ref = U.copy()
+    orc.sweep(ref, dims, nc, 1.7, 1)
+    prec = cu.FP64 if precision == "fp64" else cu.FP32
+    d = to_dev(U)
+    cu.culgt_sweep(d, cu.Params.defaults(nc, dims, precision=prec), 1)
+    got = from_dev(d, U.shape)
+    assert np.isfinite(got).all()
+    assert np.abs(got - ref).max() < (1e-14 if prec == cu.FP64 else 1e-6)
