@@ -119,15 +119,21 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-# files that define the single-lattice sweep kernels: a recorded ncu traffic
-# figure holds only while these are unchanged
-KERNEL_SOURCES = ("culgt_device.cuh", "dfloat.cuh", "kernels.cuh", "ops_impl.cuh", "anneal.cuh", "mag.cuh")
+# the files that define each family of single-lattice kernels: a recorded ncu
+# traffic figure holds only while its family's files are unchanged
+_BASE_SOURCES = ("culgt_device.cuh", "dfloat.cuh", "kernels.cuh", "ops_impl.cuh")
+KERNEL_SOURCES = {
+    "halfsweep_": _BASE_SOURCES,
+    "heatbath_": _BASE_SOURCES + ("anneal.cuh",),
+    "mag_halfsweep_": _BASE_SOURCES + ("anneal.cuh", "mag.cuh"),
+}
 
 
-def source_hash():
+def source_hash(kernel_key):
+    files = next(v for k, v in KERNEL_SOURCES.items() if kernel_key.startswith(k))
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1412_3655_gb300", "csrc")
-    for name in KERNEL_SOURCES:
+    for name in files:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -144,7 +150,7 @@ def recorded_traffic(kernel_key):
     except OSError:
         return None
     entry = rec.get(kernel_key)
-    if not entry or entry.get("source_hash") != source_hash():
+    if not entry or entry.get("source_hash") != source_hash(kernel_key):
         return None
     return entry.get("dram_bytes_per_launch")
 

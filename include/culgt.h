@@ -252,9 +252,10 @@ culgt_status culgt_plaquette(const void *d_links, const culgt_params *p, void *c
 culgt_status culgt_reunitarize(void *d_links, const culgt_params *p, void *cuda_stream);
 
 /* ---- batched API: many independent problems, one launch per phase ------
- * Problems may differ in dims; nc, precision, omega and the stopping rule
- * come from *common (its dims are ignored). Each problem converges and
- * retires on its own theta. out receives n results (may be NULL). */
+ * Problems may differ in dims; nc, precision, omega, the gauge (Landau or
+ * MAG) and the stopping rule come from *common (its dims are ignored). Each
+ * problem converges and retires on its own theta. out receives n results
+ * (may be NULL). */
 typedef struct {
     void *d_links;  /* canonical links of this problem, device, dtype_in of *common */
     int dims[4];

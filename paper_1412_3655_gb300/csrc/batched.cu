@@ -201,7 +201,10 @@ struct Engine {
     void check_phase(int phase, int only_switched, int k)
     {
         const BPhaseOps *b = phase == PH_FP32 ? b32 : b64;
-        b->theta(dp, d_theta_map, n_theta_tiles, phase, only_switched, partials, s);
+        if (cp.gauge == CULGT_MAG)
+            b->mag_theta(dp, d_theta_map, n_theta_tiles, phase, only_switched, partials, s);
+        else
+            b->theta(dp, d_theta_map, n_theta_tiles, phase, only_switched, partials, s);
         k_b_decide<<<(unsigned)hp.size(), 32, 0, s>>>(dp, partials, phase, only_switched, k, rule);
         count_launch();
     }
@@ -218,13 +221,22 @@ struct Engine {
         }
     }
 
+    // one colour of an OR half-sweep (Landau or MAG) over every problem in `phase`
+    void sweep_colour(const BPhaseOps *b, int colour, int phase, double omega, int variant, bool acc)
+    {
+        if (cp.gauge == CULGT_MAG)
+            b->mag_sweep(dp, d_sweep_map, n_sweep_tiles, colour, phase, omega, variant, acc, s);
+        else
+            b->sweep(dp, d_sweep_map, n_sweep_tiles, colour, phase, omega, variant, acc, s);
+    }
+
     // k sweeps starting after sweep n, then the check
     void body(int k, int n)
     {
         for (int j = 0; j < k; j++) {
             for (int colour = 0; colour < 2; colour++) {
-                if (has32) b32->sweep(dp, d_sweep_map, n_sweep_tiles, colour, PH_FP32, cp.omega, cp.or_variant, acc32, s);
-                if (has64) b64->sweep(dp, d_sweep_map, n_sweep_tiles, colour, PH_FP64, cp.omega, cp.or_variant, acc64, s);
+                if (has32) sweep_colour(b32, colour, PH_FP32, cp.omega, cp.or_variant, acc32);
+                if (has64) sweep_colour(b64, colour, PH_FP64, cp.omega, cp.or_variant, acc64);
             }
             if (cp.reunit_every > 0 && (n + j + 1) % cp.reunit_every == 0) {
                 if (has32) b32->reunit(dp, d_theta_map, n_theta_tiles, PH_FP32, acc32, s);
@@ -318,11 +330,14 @@ struct Engine {
                 a->steps > 1 ? a->t_start + (a->t_end - a->t_start) * (double)k / (double)(a->steps - 1) : a->t_start;
             for (int m = 0; m <= a->micro_sweeps; m++) {
                 for (int colour = 0; colour < 2; colour++) {
-                    if (m == 0)
+                    if (m == 0 && cp.gauge == CULGT_MAG)
+                        b->mag_heatbath(dp, d_sweep_map, n_sweep_tiles, colour, phase, 1.0 / T, a->seed, (uint32_t)k,
+                                        acc, s);
+                    else if (m == 0)
                         b->heatbath(dp, d_sweep_map, n_sweep_tiles, colour, phase, 1.0 / T, a->seed, (uint32_t)k, acc,
                                     s);
                     else
-                        b->sweep(dp, d_sweep_map, n_sweep_tiles, colour, phase, 2.0, 0, acc, s);
+                        sweep_colour(b, colour, phase, 2.0, 0, acc);
                 }
                 done++;
                 if (cp.reunit_every > 0 && done % cp.reunit_every == 0)
@@ -422,7 +437,6 @@ culgt_status fix_batched(const culgt_problem *problems, int n, const culgt_param
         for (int mu = 0; mu < 4; mu++) p.dims[mu] = problems[i].dims[mu];
         culgt_status st = culgt_validate(&p);
         if (st != CULGT_OK) return st;
-        if (p.gauge != CULGT_LANDAU) return CULGT_ERR_ARG;
         if (!problems[i].d_links) return CULGT_ERR_ARG;
     }
     if (cudaStreamSynchronize((cudaStream_t)cuda_stream) != cudaSuccess) {

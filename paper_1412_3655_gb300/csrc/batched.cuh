@@ -12,7 +12,7 @@
 // check to know when every problem has retired.
 #pragma once
 
-#include "anneal.cuh"
+#include "mag.cuh"
 
 namespace culgt {
 
@@ -49,47 +49,102 @@ struct BRule {
     int max_sweeps;
 };
 
+// gacc(x) <- g(x) gacc(x) for a problem's site (cb, p) in PG's storage
+// (nothing for PG = void); G converted to the accumulator's arithmetic type
+template <class PG, typename T>
+__device__ __forceinline__ void b_accumulate(const BProb &pr, int cb, int p, int want_phase, const M3<T> &G)
+{
+    if constexpr (!std::is_void<PG>::value) {
+        typedef typename PG::Real A;
+        typename PG::Chunk *gp = (typename PG::Chunk *)(want_phase == PH_FP32 ? pr.gacc32 : pr.gacc64) +
+                                 (size_t)p * PG::NCHUNK * pr.g.stride + cb;
+        M3<A> a, b, Ga;
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                Ga.re[i][j] = (A)G.re[i][j];
+                Ga.im[i][j] = (A)G.im[i][j];
+            }
+        PG::load(gp, pr.g.stride, a);
+        m3_mul_rows<0, 1>(b, Ga, a);
+        if constexpr (PG::NREAL == 18) m3_rebuild_row2(b);
+        PG::store(gp, pr.g.stride, b);
+    }
+}
+
+template <class PG, typename T>
+__device__ __forceinline__ void b_accumulate(const BProb &pr, int cb, int p, int want_phase, const Q4<T> &G)
+{
+    if constexpr (!std::is_void<PG>::value) {
+        typedef typename PG::Real A;
+        typename PG::Chunk *gp = (typename PG::Chunk *)(want_phase == PH_FP32 ? pr.gacc32 : pr.gacc64) +
+                                 (size_t)p * PG::NCHUNK * pr.g.stride + cb;
+        Q4<A> a, Ga = {{(A)G.a[0], (A)G.a[1], (A)G.a[2], (A)G.a[3]}};
+        PG::load(gp, pr.g.stride, a);
+        PG::store(gp, pr.g.stride, q_mul(Ga, a));
+    }
+}
+
 // site (cb, p) of a problem: the site update of Sec. 2 with the given
 // subgroup step on the problem's links, and for PG != void the accumulation
 // gacc(x) <- g(x) gacc(x) in PG's storage.
 template <class P, class PG, bool KEEP = KeepLinks<P>::value, class Step>
 __device__ __forceinline__ void b_site_update(const BProb &pr, int cb, int p, int want_phase, const Step &step)
 {
-    typedef typename P::Real T;
-    const Geom g = pr.g;
     typename P::Chunk *base = (typename P::Chunk *)(want_phase == PH_FP32 ? pr.links32 : pr.links64);
-    if constexpr (P::NC == 3) {
-        M3<T> G;
-        su3_update<P, KEEP, 1>(base, g, cb, p, 0, true, pr.mu_first, step, &G);
-        if constexpr (!std::is_void<PG>::value) {
-            typedef typename PG::Real A;
-            typename PG::Chunk *gp = (typename PG::Chunk *)(want_phase == PH_FP32 ? pr.gacc32 : pr.gacc64) +
-                                     (size_t)p * PG::NCHUNK * g.stride + cb;
-            M3<A> a, b, Ga;
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int j = 0; j < 3; j++) {
-                    Ga.re[i][j] = (A)G.re[i][j];
-                    Ga.im[i][j] = (A)G.im[i][j];
-                }
-            PG::load(gp, g.stride, a);
-            m3_mul_rows<0, 1>(b, Ga, a);
-            if constexpr (PG::NREAL == 18) m3_rebuild_row2(b);
-            PG::store(gp, g.stride, b);
-        }
-    } else {
-        Q4<T> G;
-        su2_update<P, 1>(base, g, cb, p, 0, true, pr.mu_first, step, &G);
-        if constexpr (!std::is_void<PG>::value) {
-            typedef typename PG::Real A;
-            typename PG::Chunk *gp = (typename PG::Chunk *)(want_phase == PH_FP32 ? pr.gacc32 : pr.gacc64) +
-                                     (size_t)p * PG::NCHUNK * g.stride + cb;
-            Q4<A> a, Ga = {{(A)G.a[0], (A)G.a[1], (A)G.a[2], (A)G.a[3]}};
-            PG::load(gp, g.stride, a);
-            PG::store(gp, g.stride, q_mul(Ga, a));
-        }
-    }
+    typename P::Link G;
+    if constexpr (P::NC == 3)
+        su3_update<P, KEEP, 1>(base, pr.g, cb, p, 0, true, pr.mu_first, step, &G);
+    else
+        su2_update<P, 1>(base, pr.g, cb, p, 0, true, pr.mu_first, step, &G);
+    b_accumulate<PG>(pr, cb, p, want_phase, G);
+}
+
+// the same for the maximally Abelian gauge (Landau problems, mu = 0..3)
+template <class P, class PG, class Step>
+__device__ __forceinline__ void b_mag_site_update(const BProb &pr, int cb, int p, int want_phase, const Step &step)
+{
+    typename P::Chunk *base = (typename P::Chunk *)(want_phase == PH_FP32 ? pr.links32 : pr.links64);
+    typename P::Link G;
+    mag_site_update<P>(base, pr.g, cb, p, step, &G);
+    b_accumulate<PG>(pr, cb, p, want_phase, G);
+}
+
+// one colour of a MAG half-sweep over every problem in want_phase
+template <class P, class PG>
+__global__ void __launch_bounds__(kSweepTile) k_b_mag_halfsweep(const BProb *probs, const int *tile_prob, int colour,
+                                                               int want_phase, double omega, int variant)
+{
+    const int tile = blockIdx.x;
+    const BProb &pr = probs[tile_prob[tile]];
+    if (pr.phase != want_phase) return;
+    const int local = (tile - pr.sweep_tile0) * kSweepTile + threadIdx.x;
+    if (local >= pr.n_cb) return;
+    const int cb = pr.cb_begin + local;
+    const int p = (colour + pr.par_off) & 1;
+    b_mag_site_update<P, PG>(pr, cb, p, want_phase, MagOrStep<typename P::Real>{(typename P::Real)omega, variant});
+}
+
+// one colour of a MAG heat-bath half-sweep; problem j draws with seed + j
+template <class P, class PG>
+__global__ void __launch_bounds__(kSweepTile) k_b_mag_heatbath(const BProb *probs, const int *tile_prob, int colour,
+                                                              int want_phase, double inv_temp,
+                                                              unsigned long long seed, uint32_t sweep)
+{
+    typedef typename P::Real T;
+    const int tile = blockIdx.x;
+    const int j = tile_prob[tile];
+    const BProb &pr = probs[j];
+    if (pr.phase != want_phase) return;
+    const int local = (tile - pr.sweep_tile0) * kSweepTile + threadIdx.x;
+    if (local >= pr.n_cb) return;
+    const int cb = pr.cb_begin + local;
+    const int p = (colour + pr.par_off) & 1;
+    const unsigned long long key = seed + (unsigned long long)j;
+    const MagHbStep<T> step{(T)(2.0 * inv_temp), (uint32_t)key, (uint32_t)(key >> 32), canonical_site(pr.g, cb, p),
+                            sweep};
+    b_mag_site_update<P, PG>(pr, cb, p, want_phase, step);
 }
 
 // One colour of an overrelaxation half-sweep over every problem in
@@ -214,6 +269,23 @@ __global__ void __launch_bounds__(kThetaTile) k_b_theta(const BProb *probs, cons
             th = 2.0 * ((double)v1 * v1 + (double)v2 * v2 + (double)v3 * v3);
             fs = 2.0 * (double)f;
         }
+    }
+    block_reduce2(th, fs, partials);
+}
+
+// per-tile partial sums of theta_MAG and F_MAG terms (Landau problems)
+template <class P>
+__global__ void __launch_bounds__(kThetaTile) k_b_mag_theta(const BProb *probs, const int *tile_prob, int want_phase,
+                                                            int only_switched, double2 *partials)
+{
+    const int tile = blockIdx.x;
+    const BProb &pr = probs[tile_prob[tile]];
+    double th = 0.0, fs = 0.0;
+    int p, cb;
+    if (b_active(pr, want_phase, only_switched) && theta_site(pr, tile, p, cb)) {
+        const typename P::Chunk *base =
+            (const typename P::Chunk *)(want_phase == PH_FP32 ? pr.links32 : pr.links64);
+        mag_site_terms<P>(base, pr.g, cb, p, th, fs);
     }
     block_reduce2(th, fs, partials);
 }

@@ -18,6 +18,13 @@ struct BPhaseOps {
                      unsigned long long seed, uint32_t sweep, bool acc, cudaStream_t s);
     void (*theta)(const BProb *probs, const int *map, int ntiles, int phase, int only_switched, double2 *partials,
                   cudaStream_t s);
+    // the maximally Abelian gauge: half-sweep colour, heat-bath colour, theta_MAG / F_MAG partials
+    void (*mag_sweep)(const BProb *probs, const int *map, int ntiles, int colour, int phase, double omega, int variant,
+                      bool acc, cudaStream_t s);
+    void (*mag_heatbath)(const BProb *probs, const int *map, int ntiles, int colour, int phase, double inv_temp,
+                         unsigned long long seed, uint32_t sweep, bool acc, cudaStream_t s);
+    void (*mag_theta)(const BProb *probs, const int *map, int ntiles, int phase, int only_switched,
+                      double2 *partials, cudaStream_t s);
     void (*reunit)(const BProb *probs, const int *map, int ntiles, int phase, bool acc, cudaStream_t s);
     // whole-lattice helpers: temporal links rotated by the accumulator; accumulator = 1
     void (*temporal)(void *links, const void *gacc, const Geom &g, cudaStream_t s);
@@ -96,6 +103,30 @@ template <class P> struct BImpl {
             k_b_heatbath<P, void><<<ntiles, kSweepTile, 0, s>>>(probs, map, colour, phase, inv_temp, seed, sweep);
         count_launch();
     }
+    static void mag_sweep(const BProb *probs, const int *map, int ntiles, int colour, int phase, double omega,
+                          int variant, bool acc, cudaStream_t s)
+    {
+        if (acc)
+            k_b_mag_halfsweep<P, PG><<<ntiles, kSweepTile, 0, s>>>(probs, map, colour, phase, omega, variant);
+        else
+            k_b_mag_halfsweep<P, void><<<ntiles, kSweepTile, 0, s>>>(probs, map, colour, phase, omega, variant);
+        count_launch();
+    }
+    static void mag_heatbath(const BProb *probs, const int *map, int ntiles, int colour, int phase, double inv_temp,
+                             unsigned long long seed, uint32_t sweep, bool acc, cudaStream_t s)
+    {
+        if (acc)
+            k_b_mag_heatbath<P, PG><<<ntiles, kSweepTile, 0, s>>>(probs, map, colour, phase, inv_temp, seed, sweep);
+        else
+            k_b_mag_heatbath<P, void><<<ntiles, kSweepTile, 0, s>>>(probs, map, colour, phase, inv_temp, seed, sweep);
+        count_launch();
+    }
+    static void mag_theta(const BProb *probs, const int *map, int ntiles, int phase, int only_switched,
+                          double2 *partials, cudaStream_t s)
+    {
+        k_b_mag_theta<P><<<ntiles, kThetaTile, 0, s>>>(probs, map, phase, only_switched, partials);
+        count_launch();
+    }
     static void theta(const BProb *probs, const int *map, int ntiles, int phase, int only_switched,
                       double2 *partials, cudaStream_t s)
     {
@@ -139,6 +170,9 @@ template <class P> struct BImpl {
         o.fp32 = kFP32;
         o.sweep = sweep;
         o.heatbath = heatbath;
+        o.mag_sweep = mag_sweep;
+        o.mag_heatbath = mag_heatbath;
+        o.mag_theta = mag_theta;
         o.theta = theta;
         o.reunit = reunit;
         o.temporal = temporal;

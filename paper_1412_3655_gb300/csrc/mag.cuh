@@ -327,77 +327,84 @@ __global__ void __launch_bounds__(128) k_mag_heatbath(typename P::Chunk *base, t
     if (acc) accumulate_gauge<P, PG>(gacc, g, parity, cb, G);
 }
 
+// theta_MAG and F_MAG terms of site (cb, p): th = sum_{i != j} |(X_i - X_j)_ij|^2,
+// fs = sum_mu sum_a |U_mu(x)_aa|^2; per-site values in the storage precision
+// (FP64 for double-float)
+template <class P>
+__device__ __forceinline__ void mag_site_terms(const typename P::Chunk *base, const Geom &g, int cb, int p, double &th,
+                                               double &fs)
+{
+    typedef typename ThetaReal<typename P::Real>::type T;
+    int x[4];
+    decode_site(g, cb, p, x);
+    if constexpr (P::NC == 3) {
+        M3<T> X[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) m3_zero(X[a]);
+        T f = T(0);
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            M3<T> u, b;
+            load_as<P>(base + plane_offset(g, p, mu, P::NCHUNK) + cb, g.stride, u);
+            load_as<P>(base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1), g.stride, b);
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                f = fma(u.re[a][a], u.re[a][a], fma(u.im[a][a], u.im[a][a], f));
+                const T ur[3] = {u.re[0][a], u.re[1][a], u.re[2][a]};
+                const T ui[3] = {u.im[0][a], u.im[1][a], u.im[2][a]};
+                herm_acc_outer(X[a], ur, ui);
+                const T wr[3] = {b.re[a][0], b.re[a][1], b.re[a][2]};
+                const T wi[3] = {-b.im[a][0], -b.im[a][1], -b.im[a][2]};
+                herm_acc_outer(X[a], wr, wi);
+            }
+        }
+        // |(X_i - X_j)_ij|^2 for i < j, twice (the (j, i) entry has the same modulus)
+        T t = T(0);
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = i + 1; j < 3; j++) {
+                const T dr = X[i].re[i][j] - X[j].re[i][j], di = X[i].im[i][j] - X[j].im[i][j];
+                t = fma(dr, dr, fma(di, di, t));
+            }
+        th = 2.0 * (double)t;
+        fs = (double)f;
+    } else {
+        T z[3] = {T(0), T(0), T(0)};
+        T f = T(0);
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            Q4<T> u, b;
+            load_as<P>(base + plane_offset(g, p, mu, P::NCHUNK) + cb, g.stride, u);
+            load_as<P>(base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1), g.stride, b);
+            f = fma(u.a[0], u.a[0], fma(u.a[3], u.a[3], f));
+            T v[3];
+            q_rotate_e3(u, v);
+            z[0] += v[0];
+            z[1] += v[1];
+            z[2] += v[2];
+            const Q4<T> bd = {{b.a[0], -b.a[1], -b.a[2], -b.a[3]}};
+            q_rotate_e3(bd, v);
+            z[0] += v[0];
+            z[1] += v[1];
+            z[2] += v[2];
+        }
+        // |Z_01|^2 + |Z_10|^2 = 2 (z1^2 + z2^2); |U_00|^2 + |U_11|^2 = 2 (a0^2 + a3^2)
+        th = 2.0 * ((double)z[0] * z[0] + (double)z[1] * z[1]);
+        fs = 2.0 * (double)f;
+    }
+}
+
 // per-block partial sums of (theta_MAG, sum_mu sum_a |U_aa|^2) over all
-// sites, one thread per site of both parities; per-site values in the
-// storage precision (FP64 for double-float), accumulated in FP64:
-// theta_site = sum_{i != j} |(X_i - X_j)_ij|^2
+// sites, one thread per site of both parities, accumulated in FP64
 template <class P>
 __global__ void __launch_bounds__(256) k_mag_theta(const typename P::Chunk *base, Geom g, double2 *partials)
 {
-    typedef typename ThetaReal<typename P::Real>::type T;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     double th = 0.0, fs = 0.0;
     if (s < 2 * g.Vh) {
         const int p = s >= g.Vh;
-        const int cb = s - p * g.Vh;
-        int x[4];
-        decode_site(g, cb, p, x);
-        if constexpr (P::NC == 3) {
-            M3<T> X[3];
-#pragma unroll
-            for (int a = 0; a < 3; a++) m3_zero(X[a]);
-            T f = T(0);
-#pragma unroll
-            for (int mu = 0; mu < 4; mu++) {
-                M3<T> u, b;
-                load_as<P>(base + plane_offset(g, p, mu, P::NCHUNK) + cb, g.stride, u);
-                load_as<P>(base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1), g.stride, b);
-#pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    f = fma(u.re[a][a], u.re[a][a], fma(u.im[a][a], u.im[a][a], f));
-                    const T ur[3] = {u.re[0][a], u.re[1][a], u.re[2][a]};
-                    const T ui[3] = {u.im[0][a], u.im[1][a], u.im[2][a]};
-                    herm_acc_outer(X[a], ur, ui);
-                    const T wr[3] = {b.re[a][0], b.re[a][1], b.re[a][2]};
-                    const T wi[3] = {-b.im[a][0], -b.im[a][1], -b.im[a][2]};
-                    herm_acc_outer(X[a], wr, wi);
-                }
-            }
-            // |(X_i - X_j)_ij|^2 for i < j, twice (the (j, i) entry has the same modulus)
-            T t = T(0);
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int j = i + 1; j < 3; j++) {
-                    const T dr = X[i].re[i][j] - X[j].re[i][j], di = X[i].im[i][j] - X[j].im[i][j];
-                    t = fma(dr, dr, fma(di, di, t));
-                }
-            th = 2.0 * (double)t;
-            fs = (double)f;
-        } else {
-            T z[3] = {T(0), T(0), T(0)};
-            T f = T(0);
-#pragma unroll
-            for (int mu = 0; mu < 4; mu++) {
-                Q4<T> u, b;
-                load_as<P>(base + plane_offset(g, p, mu, P::NCHUNK) + cb, g.stride, u);
-                load_as<P>(base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1), g.stride, b);
-                f = fma(u.a[0], u.a[0], fma(u.a[3], u.a[3], f));
-                T v[3];
-                q_rotate_e3(u, v);
-                z[0] += v[0];
-                z[1] += v[1];
-                z[2] += v[2];
-                const Q4<T> bd = {{b.a[0], -b.a[1], -b.a[2], -b.a[3]}};
-                q_rotate_e3(bd, v);
-                z[0] += v[0];
-                z[1] += v[1];
-                z[2] += v[2];
-            }
-            // |Z_01|^2 + |Z_10|^2 = 2 (z1^2 + z2^2); |U_00|^2 + |U_11|^2 = 2 (a0^2 + a3^2)
-            th = 2.0 * ((double)z[0] * z[0] + (double)z[1] * z[1]);
-            fs = 2.0 * (double)f;
-        }
+        mag_site_terms<P>(base, g, s - p * g.Vh, p, th, fs);
     }
     block_reduce2(th, fs, partials);
 }

@@ -258,3 +258,30 @@ def test_mag_fix_anneal_mixed(cu, orc, nc):
     th, F = orc.mag_theta(out, dims, nc)
     assert th < 1e-12 and F == pytest.approx(r.F, rel=1e-12)
     assert orc.plaquette(out, dims, nc) == pytest.approx(orc.plaquette(U, dims, nc), abs=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("nc", [2, 3])
+def test_batched_mag_matches_single_lattice(cu, nc, precision):
+    """MAG problems of uneven sizes in shared launches end exactly where
+    culgt_mag_fix ends for each of them; with annealing, problem j draws like
+    culgt_mag_fix_anneal with seed + j."""
+    prec = cu.FP64 if precision == "fp64" else cu.MIXED
+    cases = [((4, 4, 4, 4), 1), ((2, 4, 6, 4), 2), ((4, 4, 4, 4), 3)]
+    Us = [synth.gauge_config(dims, nc, 0.4, seed) for dims, seed in cases]
+    p = cu.Params.defaults(nc, (4, 4, 4, 4), precision=prec, check_every=5, reunit_every=50, max_sweeps=5000,
+                           gauge=cu.MAG)
+    a = cu.AnnealParams(0.6, 0.05, 10, 2, SEED)
+    for anneal in (False, True):
+        ds = [to_dev(U) for U in Us]
+        res = (cu.culgt_fix_batched_anneal(ds, [c[0] for c in cases], p, a) if anneal
+               else cu.culgt_fix_batched(ds, [c[0] for c in cases], p))
+        for j, ((dims, _), U, d, r) in enumerate(zip(cases, Us, ds, res)):
+            pj = cu.Params(**{**p.__dict__, "dims": dims})
+            e = to_dev(U)
+            rs = (cu.culgt_mag_fix_anneal(e, pj, cu.AnnealParams(0.6, 0.05, 10, 2, SEED + j)) if anneal
+                  else cu.culgt_mag_fix(e, pj))
+            assert r.status == cu.OK and rs.status == cu.OK and r.theta < 1e-12
+            assert (r.sweeps_fp32, r.sweeps_fp64) == (rs.sweeps_fp32, rs.sweeps_fp64)
+            assert r.F == pytest.approx(rs.F, rel=1e-12)
+            assert torch.allclose(d, e, atol=1e-12, rtol=0)
