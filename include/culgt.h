@@ -329,8 +329,8 @@ culgt_status culgt_mag_fix_anneal(void *d_links, const culgt_params *p, const cu
 
 /* culgt_fix_batched with the annealing schedule run on every problem first
  * (in shared launches, all problems in step). Problem j draws with the key
- * seed + j, so its draws are those of culgt_landau_fix_anneal with that
- * seed. */
+ * seed + j, so its draws are those of culgt_landau_fix_anneal (or, with
+ * common->gauge = CULGT_MAG, culgt_mag_fix_anneal) with that seed. */
 culgt_status culgt_fix_batched_anneal(const culgt_problem *problems, int n, const culgt_params *common,
                                       const culgt_anneal_params *a, void *cuda_stream, culgt_result *out);
 

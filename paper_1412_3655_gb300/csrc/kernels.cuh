@@ -16,7 +16,8 @@ namespace culgt {
 // KEEP = true holds the 8 links in registers between the gather and the
 // update (FP32 and SU(2): one read and one write of each link); KEEP = false
 // re-reads them from L1/L2 for the update (FP64 SU(3), whose 8 links would
-// need 288 registers).
+// need 288 registers). The subgroup step is a template argument: OrStep for
+// the overrelaxation of Sec. 2, HbStep (anneal.cuh) for the heat bath.
 
 template <class P> struct KeepLinks {
     static constexpr bool value = (sizeof(typename P::Real) * P::NREAL * 8 <= 4 * 12 * 8);
