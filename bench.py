@@ -25,6 +25,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -129,14 +130,22 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text):
+    """The source without comments and blank space, so that a comment edit
+    does not void a recorded figure."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.strip() for line in text.splitlines() if line.strip())
+
+
 def source_hash(kernel_key):
     files = next(v for k, v in KERNEL_SOURCES.items() if kernel_key.startswith(k))
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1412_3655_gb300", "csrc")
     for name in files:
-        with open(os.path.join(csrc, name), "rb") as f:
+        with open(os.path.join(csrc, name)) as f:
             h.update(name.encode())
-            h.update(f.read())
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 
