@@ -7,6 +7,10 @@ float64/float32 of shape (V, 4, Nc, Nc, 2). Device entry points take CUDA
 tensors and run on the current torch stream unless a stream is given; the
 host entry point takes a CPU tensor. All work happens in libculgt.so; this
 module has no fallback and raises if the library cannot be loaded.
+
+Besides Landau and Coulomb gauge fixing (Params.gauge = LANDAU) the library
+fixes the maximally Abelian gauge (gauge = MAG, culgt_mag_fix) and combines
+either with simulated annealing (AnnealParams and the *_anneal functions).
 """
 from __future__ import annotations
 
