@@ -58,6 +58,9 @@
  *   R16 MAG annealing: each subgroup draws B = C Bmax with u = c0^2 + c3^2
  *       exponential on [0, 1] (rate 2|z|/T), the two residual angles uniform;
  *       microcanonical sweeps are MAG overrelaxation at omega = 2.
+ *   R17 Coulomb annealing: each time slice runs the schedule of R11 on its
+ *       spatial links with its own checkerboard, keyed by seed + t, before
+ *       its overrelaxation; g accumulates for the temporal rotation.
  */
 #include <math.h>
 #include <stddef.h>
