@@ -188,3 +188,24 @@ def test_batched_empty_and_bad_problems_rejected(lib):
     probs[1].dims = (ctypes.c_int * 4)(4, 4, 4, 4)
     probs[1].d_links = None
     assert so.culgt_fix_batched(probs, 2, ctypes.byref(p._c()), None, None) == lib.ERR_ARG
+
+
+def test_header_enums_match_the_binding(lib):
+    """The constants of culgt.py are the values include/culgt.h declares."""
+    text = open(os.path.join(ROOT, "include", "culgt.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    vals = {k: int(v) for k, v in re.findall(r"\b(CULGT_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
+    for name in ("OK", "NOT_CONVERGED", "ERR_ARG", "ERR_DIMS", "ERR_NC", "ERR_CUDA", "ERR_OOM", "ERR_NONFINITE",
+                 "ERR_TIMEOUT", "ERR_TOO_LARGE", "FP64", "FP32", "MIXED", "MIXED_DF", "DF", "LANDAU", "MAG"):
+        assert vals["CULGT_" + name] == getattr(lib, name), name
+
+
+def test_struct_layouts_match_the_header(lib):
+    """Field order of the ctypes mirrors equals the C structs' (names in order)."""
+    text = open(os.path.join(ROOT, "include", "culgt.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    for cname, py in (("culgt_params", lib._Params), ("culgt_result", lib._Result),
+                      ("culgt_anneal_params", lib._AnnealParams), ("culgt_problem", lib._Problem)):
+        body = re.search(r"typedef struct \{([^{}]*)\}\s*" + cname + r";", text).group(1)
+        names = re.findall(r"(\w+)(?:\[\d+\])?\s*;", body)
+        assert names == [f[0] for f in py._fields_], cname
