@@ -310,3 +310,10 @@ def test_coulomb_annealing_raises_the_slice_maxima(orc):
         ann += list(orc.coulomb_fix_anneal(U.copy(), dims, 3, 0.6, 0.01, 200, 3, 40 + c, 1.7, 1e-12, 20000, 10,
                                            50)["F"])
     assert np.mean(ann) > np.mean(plain)
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_heatbath_of_a_zero_K_is_the_identity(orc, nc):
+    """k = 0 leaves every block alone (as the maximisation does, reading R4)."""
+    g = orc.heatbath_gauge(np.zeros((nc, nc)), 0.7, 1, 0, 0)
+    assert np.abs(g - np.eye(nc)).max() == 0

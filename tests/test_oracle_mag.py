@@ -349,3 +349,9 @@ def test_mag_heatbath_draws_depend_on_the_sweep_word(orc, nc):
     orc.mag_heatbath_sweep(b, dims, nc, 0.7, 21, 4)
     orc.mag_heatbath_sweep(c, dims, nc, 0.7, 21, 3)
     assert np.abs(a - b).max() > 1e-3 and np.array_equal(a, c)
+
+
+def test_mag_heatbath_of_a_zero_block_is_the_identity(orc):
+    """z = 0 (a block proportional to 1) leaves the block alone."""
+    B = orc.mag_heatbath_su2(2.5 * np.eye(2), 0.7, 1, 0, 0)
+    assert np.abs(B - np.eye(2)).max() == 0
