@@ -80,6 +80,14 @@ def _load():
         "oracle_mag_heatbath_sweep": (None, [dp, ip, i, d, u32p, ctypes.c_uint32]),
         "oracle_mag_anneal": (None, [dp, ip, i, d, d, i, i, u32p, i]),
         "oracle_mag_heatbath_su2": (None, [dp, d, u32p, ctypes.c_uint32, ctypes.c_uint32, i, dp]),
+        "oracle_sweep_bound": (None, [dp, ip, i, d, i, d, dp]),
+        "oracle_local_gauge_bound": (d, [dp, i, d, i]),
+        "oracle_hb_slack": (d, [d, d, d, u32p, ctypes.c_uint32, ctypes.c_uint32, i]),
+        "oracle_heatbath_gauge_bound": (d, [dp, i, d, u32p, ctypes.c_uint32, ctypes.c_uint32, d, dp]),
+        "oracle_mag_local_gauge_bound": (d, [dp, i, d, i]),
+        "oracle_mag_sweep_bound": (None, [dp, ip, i, d, i, d, dp]),
+        "oracle_heatbath_sweep_bound": (None, [dp, ip, i, d, u32p, ctypes.c_uint32, d, dp, dp]),
+        "oracle_mag_heatbath_sweep_bound": (None, [dp, ip, i, d, u32p, ctypes.c_uint32, d, dp]),
         "oracle_set_threads": (None, [i]),
         "oracle_get_threads": (i, []),
     }
@@ -368,3 +376,84 @@ def mag_heatbath_su2(Z, T, seed, site, sweep, sub=0):
     B = np.zeros((2, 2), dtype=np.complex128)
     _load().oracle_mag_heatbath_su2(_dp(Z), float(T), _key(seed), int(site), int(sweep), int(sub), _dp(B))
     return B
+
+
+# --- first-order error bounds of one sweep (for comparing another implementation) ---
+
+def _bound_array(e, V):
+    if e is None:
+        return np.ones((V, 4))
+    e = np.ascontiguousarray(e, dtype=np.float64).copy()
+    if e.shape != (V, 4):
+        raise ValueError(f"e must have shape {(V, 4)}")
+    return e
+
+
+def sweep_bound(U, L, nc, omega, variant=0, e=None, rho=1.0):
+    """One overrelaxation sweep, in place, exactly as sweep(); returns the
+    first-order bound (V, 4) on how far each output link can move when every
+    input link carries the error in e (default: one unit each) and every
+    rounding step of the sweep is charged rho units."""
+    _check_links(U, L, nc)
+    e = _bound_array(e, U.shape[0])
+    _load().oracle_sweep_bound(_dp(U), _dims(L), nc, float(omega), int(variant), float(rho), _dp(e))
+    return e
+
+
+def mag_sweep_bound(U, L, nc, omega, variant=0, e=None, rho=1.0):
+    """One MAG sweep, in place, with the bounds of sweep_bound."""
+    _check_links(U, L, nc)
+    e = _bound_array(e, U.shape[0])
+    _load().oracle_mag_sweep_bound(_dp(U), _dims(L), nc, float(omega), int(variant), float(rho), _dp(e))
+    return e
+
+
+def heatbath_sweep_bound(U, L, nc, T, seed, sweep, e=None, rho=1.0):
+    """One heat-bath sweep, in place, exactly as heatbath_sweep(); returns
+    (e, slack): the bounds of sweep_bound and, per site, the smallest slack
+    of its draws' decisions (margin over its own error bound, in units of
+    the per-step charge): an implementation whose unit roundoff exceeds the
+    slack may take that decision the other way."""
+    _check_links(U, L, nc)
+    e = _bound_array(e, U.shape[0])
+    slack = np.full(U.shape[0], np.inf)
+    _load().oracle_heatbath_sweep_bound(_dp(U), _dims(L), nc, float(T), _key(seed), int(sweep), float(rho),
+                                        _dp(e), _dp(slack))
+    return e, slack
+
+
+def mag_heatbath_sweep_bound(U, L, nc, T, seed, sweep, e=None, rho=1.0):
+    """One MAG heat-bath sweep, in place, with the bounds of sweep_bound."""
+    _check_links(U, L, nc)
+    e = _bound_array(e, U.shape[0])
+    _load().oracle_mag_heatbath_sweep_bound(_dp(U), _dims(L), nc, float(T), _key(seed), int(sweep), float(rho),
+                                            _dp(e))
+    return e
+
+
+def local_gauge_bound(K, omega, variant=0):
+    """First-order bound on ||dg|| per unit ||dK|| for the site transformation of K."""
+    K = np.ascontiguousarray(K, dtype=np.complex128)
+    return float(_load().oracle_local_gauge_bound(_dp(K), K.shape[0], float(omega), int(variant)))
+
+
+def mag_local_gauge_bound(X, omega, variant=0):
+    """First-order bound on ||dg|| per unit max_a ||dX_a|| for the MAG site transformation."""
+    X = np.ascontiguousarray(X, dtype=np.complex128)
+    return float(_load().oracle_mag_local_gauge_bound(_dp(X), X.shape[-1], float(omega), int(variant)))
+
+
+def hb_slack(alpha, dalpha, T, seed, site, sweep, sub=0):
+    """Decision slack of one heat-bath draw whose alpha is known to within dalpha."""
+    return float(_load().oracle_hb_slack(float(alpha), float(dalpha), float(T), _key(seed), int(site), int(sweep),
+                                         int(sub)))
+
+
+def heatbath_gauge_bound(K, T, seed, site, sweep, dK=1e-7):
+    """(bound on ||dg|| per unit ||dK|| of the heat-bath site transformation
+    with its draws' decisions held, smallest decision slack for errors up to dK)."""
+    K = np.ascontiguousarray(K, dtype=np.complex128)
+    sl = ctypes.c_double()
+    b = _load().oracle_heatbath_gauge_bound(_dp(K), K.shape[0], float(T), _key(seed), int(site), int(sweep),
+                                            float(dK), ctypes.byref(sl))
+    return float(b), sl.value

@@ -234,6 +234,94 @@ static void put_mat(double *G, int nc, long k, const mat *A)
 }
 
 /* ------------------------------------------------------------------ */
+/* first-order error bounds (for comparing another implementation)     */
+/* ------------------------------------------------------------------ */
+
+/* How far one sweep can move each link when its input links and its
+ * arithmetic carry small errors. Nothing here changes the sweep; it runs
+ * beside it and only sets per-link tolerances when another implementation
+ * of the same sweep, rounding differently, is compared with this one. The
+ * local problem of Sec. 2 amplifies such differences by the inverse length of
+ * the block quaternion it normalises (and the MAG problem by that of the
+ * smallest rotation); these bounds say by how much, site by site.
+ *
+ * Norms: Frobenius for matrices (||.||), Euclidean for quaternions (|.|).
+ * Facts used, all to first order in the errors:
+ *   F1  a 2x2 block w and its quaternion part a: |da| <= ||dw|| / sqrt2 (the
+ *       quaternion part is an orthogonal projection, ||q|| = sqrt2 |a|);
+ *   F2  a unit quaternion a/|a| moves by at most |da| / |a|, tangentially
+ *       (perpendicular to a);
+ *   F3  a change dr of an SU(2) element is |dr| times a unitary 2x2 matrix
+ *       (the quaternion matrix of dr / |dr|), so in a 3x3 embedding R
+ *       ||dR|| = sqrt2 |dr|, and ||dR K|| = |dr| ||rows i, j of K||;
+ *   F4  with unitary factors, ||d(A B)|| <= ||dA|| + ||dB||;
+ *   F5  a tangent change of R is dR = dB R with dB in su(2) (rows and columns
+ *       i, j), so R X R^+ moves by the commutator [dB, R X R^+], which the
+ *       multiple of 1 in R X R^+ does not reach: at most 2 |dr| times the
+ *       rows i, j of R X R^+ - l 1 for any real l.
+ * Each arithmetic step that rounds is charged rho, the unit of the bound. */
+typedef struct {
+    double *e;     /* per link, V x 4: bound on ||dU_mu(x)||, updated in place */
+    double *slack; /* per site, or NULL: smallest decision slack of the heat bath */
+    double rho;    /* charge per rounding step */
+} bound_ctx;
+
+typedef struct {
+    double E;     /* bound on the error of the running K (Landau) or of each X_a (MAG) */
+    double dg;    /* bound on ||dg|| of the site transformation so far */
+    double rho;
+    double slack; /* smallest decision slack so far (+inf: none) */
+} bound_track;
+
+static const double SQRT2 = 1.4142135623730951;
+
+/* One subgroup step whose SU(2) element moves tangentially by `amp` per
+ * unit error of the running matrix, plus one rounding charge: the running
+ * matrix's error grows by |dr| times `rows` for the tangent part and times
+ * `rows_rho` for the rounding (F3: for Landau both are the Frobenius norm of
+ * the rows i, j the step rotates; for MAG F5 and twice the rows of X_a), the
+ * site transformation's by sqrt2 |dr| (F3, F4). */
+static void track_step2(bound_track *bt, double amp, double rows, double rows_rho)
+{
+    double d = isinf(amp) ? INFINITY : amp * bt->E;
+    bt->E += rows * d + rows_rho * bt->rho;
+    bt->dg += SQRT2 * (d + bt->rho);
+}
+
+static void track_step(bound_track *bt, double amp, double rows) { track_step2(bt, amp, rows, rows); }
+
+/* ||rows i, j of A|| */
+static double rows_norm(const mat *A, int i, int j)
+{
+    double s = 0.0;
+    for (int b = 0; b < A->n; b++) s += c_abs2(A->m[i][b]) + c_abs2(A->m[j][b]);
+    return sqrt(s);
+}
+
+/* Lipschitz factor of r -> r^omega at the unit quaternion r (R3) for
+ * changes dr tangent to the unit sphere (F2). Variant 0: r^omega = v / |v|
+ * with v = (1 - omega) e0 + beta(c0) r, beta = omega (1 + (omega - 1)(c0 - 1)),
+ * so dv = beta dr + omega (omega - 1) dc0 r, the two terms perpendicular, with
+ * |dc0| <= sqrt(1 - c0^2) |dr| for tangent dr; v / |v| moves by at most
+ * |dv| / |v|. Variant 1: (cos(omega phi), n sin(omega phi)) moves by omega per
+ * unit of phi and by |sin(omega phi)| / sin(phi) per unit of the axis n. */
+static double or_lipschitz(const mat *r, double omega, int variant)
+{
+    double c0 = 0.5 * mat_trace(r).re;
+    double n2 = 0.5 * (c_abs2(r->m[0][0]) + c_abs2(r->m[0][1]) + c_abs2(r->m[1][0]) + c_abs2(r->m[1][1]));
+    double s = sqrt(fmax(n2 - c0 * c0, 0.0));
+    if (variant == 0) {
+        double beta = omega * (1.0 + (omega - 1.0) * (c0 - 1.0));
+        double v0 = (1.0 - omega) + beta * c0;
+        double nv = sqrt(v0 * v0 + beta * beta * s * s);
+        double t = omega * (omega - 1.0) * s;
+        return nv > 0.0 ? sqrt(beta * beta + t * t) / nv : INFINITY;
+    }
+    if (!(s > 0.0)) return c0 > 0.0 ? omega : INFINITY;
+    return fmax(omega, fabs(sin(omega * atan2(s, c0))) / s);
+}
+
+/* ------------------------------------------------------------------ */
 /* local maximisation, Sec. 2                                          */
 /* ------------------------------------------------------------------ */
 
@@ -301,15 +389,25 @@ static mat overrelax(const mat *g, double omega, int variant)
     }
 }
 
+/* |a| of the quaternion part of a 2x2 block: sqrt(det P(w)) */
+static double block_norm(const mat *w)
+{
+    mat q = su2_part(w);
+    return sqrt(fmax(mat_det2(&q).re, 0.0));
+}
+
 /* The overrelaxed local gauge transformation g(x) for the gathered K(x).
  * SU(2): g = (K^+/sqrt(det K^+))^omega.  SU(3): iterate over the SU(2)
  * subgroups (R1), each hit maximising Re tr[r w] on its 2x2 block of the
- * running K and then overrelaxed. */
-static mat local_gauge(const mat *K, double omega, int variant)
+ * running K and then overrelaxed. bt (or NULL) tracks the error bound: the
+ * maximiser moves by |da| / |a| <= E / (sqrt2 |a|) (F1, F2), times the
+ * overrelaxation's Lipschitz factor. */
+static mat local_gauge_b(const mat *K, double omega, int variant, bound_track *bt)
 {
     int n = K->n;
     if (n == 2) {
         mat r = su2_local_max(K);
+        if (bt) track_step(bt, or_lipschitz(&r, omega, variant) / (SQRT2 * block_norm(K)), 0.0);
         return overrelax(&r, omega, variant);
     }
     static const int sub[3][2] = {{0, 1}, {0, 2}, {1, 2}};
@@ -323,6 +421,7 @@ static mat local_gauge(const mat *K, double omega, int variant)
         w.m[1][0] = Kr.m[j][i];
         w.m[1][1] = Kr.m[j][j];
         mat r = su2_local_max(&w);
+        if (bt) track_step(bt, or_lipschitz(&r, omega, variant) / (SQRT2 * block_norm(&w)), rows_norm(&Kr, i, j));
         r = overrelax(&r, omega, variant);
         mat R = mat_identity(3);
         R.m[i][i] = r.m[0][0];
@@ -334,6 +433,8 @@ static mat local_gauge(const mat *K, double omega, int variant)
     }
     return g;
 }
+
+static mat local_gauge(const mat *K, double omega, int variant) { return local_gauge_b(K, omega, variant, NULL); }
 
 /* ------------------------------------------------------------------ */
 /* the checkerboard sweep, Sec. 2                                      */
@@ -353,13 +454,44 @@ static mat gather_K(const double *U, const lattice *lat, int nc, long i, int mu_
     return K;
 }
 
+/* Error bound of a site's local problem: its running matrix starts with
+ * the errors of the 2 (4 - mu_first) links it gathers, times `weight` (1 for
+ * K; 2 for each X_a of MAG, whose terms U P U^+ move by twice the link), plus
+ * one rounding charge. */
+static bound_track track_begin(const bound_ctx *bc, const lattice *lat, long i, int mu_first, double weight)
+{
+    bound_track bt;
+    double s = 0.0;
+    for (int mu = mu_first; mu < 4; mu++)
+        s += bc->e[(size_t)i * 4 + mu] + bc->e[(size_t)site_shift(lat, i, mu, -1) * 4 + mu];
+    bt.E = weight * s + bc->rho;
+    bt.dg = 0.0;
+    bt.rho = bc->rho;
+    bt.slack = INFINITY;
+    return bt;
+}
+
+/* After the site's update: each of its links moved by at most the error of
+ * g plus one rounding (F5); the decision slack is recorded per site. */
+static void track_end(const bound_ctx *bc, const bound_track *bt, const lattice *lat, long i, int mu_first)
+{
+    for (int mu = mu_first; mu < 4; mu++) {
+        bc->e[(size_t)i * 4 + mu] += bt->dg + bc->rho;
+        bc->e[(size_t)site_shift(lat, i, mu, -1) * 4 + mu] += bt->dg + bc->rho;
+    }
+    if (bc->slack) bc->slack[i] = bt->slack;
+}
+
 /* One site update: U_mu(x) <- g U_mu(x), U_mu(x-mu) <- U_mu(x-mu) g^+,
- * i.e. the gauge transformation of Sec. 2 with g = 1 at every other site. */
-static void update_site(double *U, const lattice *lat, int nc, long i, int mu_first,
-                        double omega, int variant, double *gacc)
+ * i.e. the gauge transformation of Sec. 2 with g = 1 at every other site.
+ * bc (or NULL) carries the error bounds along. */
+static void update_site_b(double *U, const lattice *lat, int nc, long i, int mu_first,
+                          double omega, int variant, double *gacc, const bound_ctx *bc)
 {
     mat K = gather_K(U, lat, nc, i, mu_first);
-    mat g = local_gauge(&K, omega, variant);
+    bound_track bt;
+    if (bc) bt = track_begin(bc, lat, i, mu_first, 1.0);
+    mat g = local_gauge_b(&K, omega, variant, bc ? &bt : NULL);
     mat gd = mat_adj(&g);
     for (int mu = mu_first; mu < 4; mu++) {
         long ib = site_shift(lat, i, mu, -1);
@@ -370,11 +502,18 @@ static void update_site(double *U, const lattice *lat, int nc, long i, int mu_fi
         put_link(U, nc, i, mu, &fn);
         put_link(U, nc, ib, mu, &bn);
     }
+    if (bc) track_end(bc, &bt, lat, i, mu_first);
     if (gacc) {
         mat a = get_mat(gacc, nc, i);
         mat an = mat_mul(&g, &a);
         put_mat(gacc, nc, i, &an);
     }
+}
+
+static void update_site(double *U, const lattice *lat, int nc, long i, int mu_first,
+                        double omega, int variant, double *gacc)
+{
+    update_site_b(U, lat, nc, i, mu_first, omega, variant, gacc, NULL);
 }
 
 static int site_parity(const lattice *lat, long i, int mu_first)
@@ -402,6 +541,21 @@ void oracle_sweep(double *U, const int *L, int nc, double omega, int variant, in
     for (int s = 0; s < n_sweeps; s++) {
         oracle_halfsweep(U, L, nc, 0, omega, variant);
         oracle_halfsweep(U, L, nc, 1, omega, variant);
+    }
+}
+
+/* One sweep, exactly as oracle_sweep, carrying the first-order error bounds
+ * along: e (V x 4) holds a bound on each input link's error on entry and on
+ * each output link's on return, in units of rho (the charge per rounding
+ * step; rho = 0 propagates the input errors alone). */
+void oracle_sweep_bound(double *U, const int *L, int nc, double omega, int variant, double rho, double *e)
+{
+    lattice lat = make_lattice(L);
+    bound_ctx bc = {e, NULL, rho};
+    for (int parity = 0; parity < 2; parity++) {
+#pragma omp parallel for schedule(static)
+        for (long i = 0; i < lat.V; i++)
+            if (site_parity(&lat, i, 0) == parity) update_site_b(U, &lat, nc, i, 0, omega, variant, NULL, &bc);
     }
 }
 
@@ -825,33 +979,97 @@ static const double TWO_PI = 6.283185307179586;
  * 1 - x0^2 = delta eps. After HB_MAX_ATTEMPTS rejections (below 1e-16 at any
  * alpha) the draw gives delta = 0, eps = 2. *attempts receives the number of
  * attempts made. */
+/* Attempt a of the draw: the candidate delta and eps, and the two sides of
+ * its acceptance test (kept when lhs <= rhs). */
+static void hb_attempt(double alpha, const uint32_t *key, uint32_t site, uint32_t sweep, int sub, int a,
+                       double *delta, double *eps, double *lhs, double *rhs)
+{
+    double u[4];
+    draw4(key, site, sweep, ((uint32_t)a << 4) | ((uint32_t)sub << 1), u);
+    if (alpha < HB_CREUTZ_BELOW) {
+        double d = -log1p(u[0] * expm1(-2.0 * alpha)) / alpha;
+        double e = log1p((1.0 - u[0]) * expm1(2.0 * alpha)) / alpha;
+        *delta = d;
+        *eps = e;
+        *lhs = u[1] * u[1];
+        *rhs = d * e;
+    } else {
+        double c = cos(TWO_PI * u[1]);
+        double d = -(log(u[0]) + c * c * log(u[2])) / alpha;
+        *delta = d;
+        *eps = 2.0 - d;
+        *lhs = u[3] * u[3];
+        *rhs = 1.0 - 0.5 * d;
+    }
+}
+
 static void hb_draw(double alpha, const uint32_t *key, uint32_t site, uint32_t sweep, int sub, double *delta,
                     double *eps, int *attempts)
 {
     for (int a = 0; a < HB_MAX_ATTEMPTS; a++) {
-        double u[4];
-        draw4(key, site, sweep, ((uint32_t)a << 4) | ((uint32_t)sub << 1), u);
+        double d, e, lhs, rhs;
+        hb_attempt(alpha, key, site, sweep, sub, a, &d, &e, &lhs, &rhs);
         if (attempts) *attempts = a + 1;
-        if (alpha < HB_CREUTZ_BELOW) {
-            double d = -log1p(u[0] * expm1(-2.0 * alpha)) / alpha;
-            double e = log1p((1.0 - u[0]) * expm1(2.0 * alpha)) / alpha;
-            if (u[1] * u[1] <= d * e) {
-                *delta = d;
-                *eps = e;
-                return;
-            }
-        } else {
-            double c = cos(TWO_PI * u[1]);
-            double d = -(log(u[0]) + c * c * log(u[2])) / alpha;
-            if (u[3] * u[3] <= 1.0 - 0.5 * d) {
-                *delta = d;
-                *eps = 2.0 - d;
-                return;
-            }
+        if (lhs <= rhs) {
+            *delta = d;
+            *eps = e;
+            return;
         }
     }
     *delta = 0.0;
     *eps = 2.0;
+}
+
+/* Relative step of the central differences in alpha (or beta) below: large
+ * enough that rounding (1e-16 / 1e-6) stays far below the derivative, small
+ * enough that the second-order remainder does too. */
+#define FD_STEP 1e-6
+
+/* Error bound of one heat-bath subgroup draw (R7, R10) at alpha = 2 k / T
+ * when the block is known to within E (Frobenius). The maximiser v moves by
+ * E / (sqrt2 k) (F1, F2); alpha moves by 2 |dk| / T <= sqrt2 E / T, and x with
+ * it by |dx/dalpha| per unit (a central difference of the accepted attempt's
+ * (delta, sqrt(delta eps)) with the same uniforms); r = x v moves by the sum.
+ * A decision whose two sides differ by less than their own error may go the
+ * other way in another implementation: for every attempt made, and for the
+ * choice of method at alpha = 2, the decision slack is the margin divided by
+ * that error (16 rounding charges for the compared values plus the margin's
+ * sensitivity to alpha times alpha's error); a slack below the unit roundoff
+ * of an implementation marks a decision it may take differently. */
+static void hb_track(bound_track *bt, double k, double alpha, double inv_T, const uint32_t *key, uint32_t site,
+                     uint32_t sweep, int sub, double rows)
+{
+    double dalpha = SQRT2 * inv_T * bt->E; /* bound on alpha's error */
+    double sl = fabs(alpha - HB_CREUTZ_BELOW) / (4.0 * bt->rho * alpha + dalpha);
+    double xprime = 0.0;
+    double h = FD_STEP * alpha;
+    for (int a = 0; a < HB_MAX_ATTEMPTS; a++) {
+        double d, e, lhs, rhs, dp, ep, lp, rp, dm, em, lm, rm;
+        hb_attempt(alpha, key, site, sweep, sub, a, &d, &e, &lhs, &rhs);
+        hb_attempt(alpha + h, key, site, sweep, sub, a, &dp, &ep, &lp, &rp);
+        hb_attempt(alpha - h, key, site, sweep, sub, a, &dm, &em, &lm, &rm);
+        double mprime = fabs((lp - rp) - (lm - rm)) / (2.0 * h);
+        sl = fmin(sl, fabs(lhs - rhs) / (16.0 * bt->rho + mprime * dalpha));
+        if (lhs <= rhs) {
+            double dd = (dp - dm) / (2.0 * h);
+            double ds = (sqrt(fmax(dp * ep, 0.0)) - sqrt(fmax(dm * em, 0.0))) / (2.0 * h);
+            xprime = sqrt(dd * dd + ds * ds);
+            break;
+        }
+    }
+    bt->slack = fmin(bt->slack, sl);
+    track_step(bt, (1.0 / k + xprime * 2.0 * inv_T) / SQRT2, rows);
+}
+
+/* The decision slack of hb_track for one draw whose alpha is known to
+ * within dalpha (no rounding charges): below 1, some alpha within dalpha may
+ * take one of the draw's decisions the other way. */
+double oracle_hb_slack(double alpha, double dalpha, double T, const uint32_t *key, uint32_t site, uint32_t sweep,
+                       int sub)
+{
+    bound_track bt = {dalpha * T / SQRT2, 0.0, 0.0, INFINITY};
+    hb_track(&bt, 0.5 * alpha * T, alpha, 1.0 / T, key, site, sweep, sub, 0.0);
+    return bt.slack;
 }
 
 double oracle_hb_delta(double alpha, const uint32_t *key, uint32_t site, uint32_t sweep, int sub, int *attempts)
@@ -897,11 +1115,16 @@ static mat quaternion_matrix(const double *x)
  * weight exp(Re tr[r w] / T) over Haar measure is that of x0 above with
  * alpha = 2 k / T and a uniform direction. r = x v, rescaled to det r = 1.
  * k = 0 leaves the block alone (as R4). */
-static mat heatbath_su2(const mat *w, double inv_T, const uint32_t *key, uint32_t site, uint32_t sweep, int sub)
+static mat heatbath_su2(const mat *w, double inv_T, const uint32_t *key, uint32_t site, uint32_t sweep, int sub,
+                        bound_track *bt, double rows)
 {
     mat q = su2_part(w);
     double k = sqrt(mat_det2(&q).re);
-    if (!(k > 0.0)) return mat_identity(2);
+    if (!(k > 0.0)) {
+        if (bt) track_step(bt, INFINITY, rows);
+        return mat_identity(2);
+    }
+    if (bt) hb_track(bt, k, (2.0 * k) * inv_T, inv_T, key, site, sweep, sub, rows);
     mat v = su2_local_max(w);
     double x[4];
     oracle_hb_x((2.0 * k) * inv_T, key, site, sweep, sub, x);
@@ -916,10 +1139,11 @@ static mat heatbath_su2(const mat *w, double inv_T, const uint32_t *key, uint32_
 
 /* The heat-bath gauge transformation of one site: SU(2) directly, SU(3)
  * over the subgroups of R1 with the running K, as in local_gauge. */
-static mat heatbath_gauge(const mat *K, double inv_T, const uint32_t *key, uint32_t site, uint32_t sweep)
+static mat heatbath_gauge(const mat *K, double inv_T, const uint32_t *key, uint32_t site, uint32_t sweep,
+                          bound_track *bt)
 {
     int n = K->n;
-    if (n == 2) return heatbath_su2(K, inv_T, key, site, sweep, 0);
+    if (n == 2) return heatbath_su2(K, inv_T, key, site, sweep, 0, bt, 0.0);
     static const int sub[3][2] = {{0, 1}, {0, 2}, {1, 2}};
     mat Kr = *K;
     mat g = mat_identity(3);
@@ -930,7 +1154,7 @@ static mat heatbath_gauge(const mat *K, double inv_T, const uint32_t *key, uint3
         w.m[0][1] = Kr.m[i][j];
         w.m[1][0] = Kr.m[j][i];
         w.m[1][1] = Kr.m[j][j];
-        mat r = heatbath_su2(&w, inv_T, key, site, sweep, s);
+        mat r = heatbath_su2(&w, inv_T, key, site, sweep, s, bt, rows_norm(&Kr, i, j));
         mat R = mat_identity(3);
         R.m[i][i] = r.m[0][0];
         R.m[i][j] = r.m[0][1];
@@ -942,11 +1166,13 @@ static mat heatbath_gauge(const mat *K, double inv_T, const uint32_t *key, uint3
     return g;
 }
 
-static void heatbath_site(double *U, const lattice *lat, int nc, long i, int mu_first, double inv_T,
-                          const uint32_t *key, uint32_t sweep, double *gacc)
+static void heatbath_site_b(double *U, const lattice *lat, int nc, long i, int mu_first, double inv_T,
+                            const uint32_t *key, uint32_t sweep, double *gacc, const bound_ctx *bc)
 {
     mat K = gather_K(U, lat, nc, i, mu_first);
-    mat g = heatbath_gauge(&K, inv_T, key, (uint32_t)i, sweep);
+    bound_track bt;
+    if (bc) bt = track_begin(bc, lat, i, mu_first, 1.0);
+    mat g = heatbath_gauge(&K, inv_T, key, (uint32_t)i, sweep, bc ? &bt : NULL);
     mat gd = mat_adj(&g);
     for (int mu = mu_first; mu < 4; mu++) {
         long ib = site_shift(lat, i, mu, -1);
@@ -957,11 +1183,18 @@ static void heatbath_site(double *U, const lattice *lat, int nc, long i, int mu_
         put_link(U, nc, i, mu, &fn);
         put_link(U, nc, ib, mu, &bn);
     }
+    if (bc) track_end(bc, &bt, lat, i, mu_first);
     if (gacc) {
         mat a = get_mat(gacc, nc, i);
         mat an = mat_mul(&g, &a);
         put_mat(gacc, nc, i, &an);
     }
+}
+
+static void heatbath_site(double *U, const lattice *lat, int nc, long i, int mu_first, double inv_T,
+                          const uint32_t *key, uint32_t sweep, double *gacc)
+{
+    heatbath_site_b(U, lat, nc, i, mu_first, inv_T, key, sweep, gacc, NULL);
 }
 
 /* One heat-bath sweep at temperature T (black, then white; Landau, mu =
@@ -982,6 +1215,22 @@ void oracle_heatbath_sweep(double *U, const int *L, int nc, double T, const uint
 {
     oracle_heatbath_halfsweep(U, L, nc, 0, T, key, sweep, gacc);
     oracle_heatbath_halfsweep(U, L, nc, 1, T, key, sweep, gacc);
+}
+
+/* One heat-bath sweep, exactly as oracle_heatbath_sweep, with the error
+ * bounds of oracle_sweep_bound in e (V x 4) and each site's smallest
+ * decision slack in slack (V). */
+void oracle_heatbath_sweep_bound(double *U, const int *L, int nc, double T, const uint32_t *key, uint32_t sweep,
+                                 double rho, double *e, double *slack)
+{
+    lattice lat = make_lattice(L);
+    bound_ctx bc = {e, slack, rho};
+    double inv_T = 1.0 / T;
+    for (int parity = 0; parity < 2; parity++) {
+#pragma omp parallel for schedule(static)
+        for (long i = 0; i < lat.V; i++)
+            if (site_parity(&lat, i, 0) == parity) heatbath_site_b(U, &lat, nc, i, 0, inv_T, key, sweep, NULL, &bc);
+    }
 }
 
 /* Microcanonical sweep: overrelaxation at omega = 2, r -> r^2 for the
@@ -1077,7 +1326,38 @@ static mat mag_su2_max(const mat *Z)
 /* R14: the MAG site transformation: SU(2) directly, SU(3) over the subgroups
  * of R1, each maximising its block and overrelaxed (R3), the running X_a
  * rotated by every subgroup update (X_a <- R X_a R^+, g <- R g). */
-static mat mag_local_gauge(mat *X, int nc, double omega, int variant)
+/* Error bound of the MAG maximiser of a block Z whose X_a are known to
+ * within E: z moves by at most ||dZ|| <= 2 E, and the smallest rotation
+ * (|z| + z3, -z2, z1, 0) / N, N = sqrt(2 |z| (|z| + z3)), depends on z / |z|
+ * alone, so it moves by |dz| / N (an unnormalised vector that moves as
+ * z / |z| does, over its length sqrt(2 (1 + z3 / |z|))). Returns 2 / N. */
+static double mag_max_amp(const mat *Z)
+{
+    double z3 = 0.5 * (Z->m[0][0].re - Z->m[1][1].re);
+    double z1 = Z->m[0][1].re, z2 = -Z->m[0][1].im;
+    double n = sqrt(z1 * z1 + z2 * z2 + z3 * z3);
+    double N = sqrt(fmax(2.0 * n * (n + z3), 0.0));
+    return N > 0.0 ? 2.0 / N : INFINITY;
+}
+
+/* X_a <- R X_a R^+ moves by at most this per unit of |dr|: for a tangent
+ * change (shifted = 1) 2 max_a ||rows i, j of X_a - l_a 1|| with l_a the mean
+ * of the diagonal entries i, j (F5), for any change 2 max_a ||rows i, j of X_a|| (F3) */
+static double mag_rows(const mat *X, int nc, int i, int j, int shifted)
+{
+    double m = 0.0;
+    for (int a = 0; a < nc; a++) {
+        mat Y = X[a];
+        if (shifted) {
+            double l = 0.5 * (X[a].m[i][i].re + X[a].m[j][j].re);
+            for (int b = 0; b < nc; b++) Y.m[b][b].re -= l;
+        }
+        m = fmax(m, rows_norm(&Y, i, j));
+    }
+    return 2.0 * m;
+}
+
+static mat mag_local_gauge_b(mat *X, int nc, double omega, int variant, bound_track *bt)
 {
     static const int sub[3][2] = {{0, 1}, {0, 2}, {1, 2}};
     int nsub = nc == 2 ? 1 : 3;
@@ -1091,6 +1371,9 @@ static mat mag_local_gauge(mat *X, int nc, double omega, int variant)
         Z.m[1][0] = D.m[j][i];
         Z.m[1][1] = D.m[j][j];
         mat r = mag_su2_max(&Z);
+        if (bt)
+            track_step2(bt, or_lipschitz(&r, omega, variant) * mag_max_amp(&Z), mag_rows(X, nc, i, j, 1),
+                        mag_rows(X, nc, i, j, 0));
         r = overrelax(&r, omega, variant);
         mat R = mat_identity(nc);
         R.m[i][i] = r.m[0][0];
@@ -1107,11 +1390,22 @@ static mat mag_local_gauge(mat *X, int nc, double omega, int variant)
     return g;
 }
 
-static void mag_update_site(double *U, const lattice *lat, int nc, long i, double omega, int variant)
+static mat mag_local_gauge(mat *X, int nc, double omega, int variant)
+{
+    return mag_local_gauge_b(X, nc, omega, variant, NULL);
+}
+
+/* The MAG site update; bc (or NULL) carries the error bounds: each X_a
+ * starts with twice the gathered links' errors (U P U^+ moves by 2 ||dU||)
+ * and is rotated on both sides by each subgroup step (nK = 2 x 8, F4). */
+static void mag_update_site_b(double *U, const lattice *lat, int nc, long i, double omega, int variant,
+                              const bound_ctx *bc)
 {
     mat X[3];
     mag_X(U, lat, nc, i, X);
-    mat g = mag_local_gauge(X, nc, omega, variant);
+    bound_track bt;
+    if (bc) bt = track_begin(bc, lat, i, 0, 2.0);
+    mat g = mag_local_gauge_b(X, nc, omega, variant, bc ? &bt : NULL);
     mat gd = mat_adj(&g);
     for (int mu = 0; mu < 4; mu++) {
         long ib = site_shift(lat, i, mu, -1);
@@ -1122,6 +1416,12 @@ static void mag_update_site(double *U, const lattice *lat, int nc, long i, doubl
         put_link(U, nc, i, mu, &fn);
         put_link(U, nc, ib, mu, &bn);
     }
+    if (bc) track_end(bc, &bt, lat, i, 0);
+}
+
+static void mag_update_site(double *U, const lattice *lat, int nc, long i, double omega, int variant)
+{
+    mag_update_site_b(U, lat, nc, i, omega, variant, NULL);
 }
 
 void oracle_mag_halfsweep(double *U, const int *L, int nc, int parity, double omega, int variant)
@@ -1137,6 +1437,19 @@ void oracle_mag_sweep(double *U, const int *L, int nc, double omega, int variant
     for (int s = 0; s < n_sweeps; s++) {
         oracle_mag_halfsweep(U, L, nc, 0, omega, variant);
         oracle_mag_halfsweep(U, L, nc, 1, omega, variant);
+    }
+}
+
+/* One MAG sweep, exactly as oracle_mag_sweep, with the error bounds of
+ * oracle_sweep_bound. */
+void oracle_mag_sweep_bound(double *U, const int *L, int nc, double omega, int variant, double rho, double *e)
+{
+    lattice lat = make_lattice(L);
+    bound_ctx bc = {e, NULL, rho};
+    for (int parity = 0; parity < 2; parity++) {
+#pragma omp parallel for schedule(static)
+        for (long i = 0; i < lat.V; i++)
+            if (site_parity(&lat, i, 0) == parity) mag_update_site_b(U, &lat, nc, i, omega, variant, &bc);
     }
 }
 
@@ -1209,6 +1522,16 @@ void oracle_mag_local_gauge(double *X, int nc, double omega, int variant, double
     put_mat(g, nc, 0, &r);
 }
 
+/* The bound of mag_local_gauge_b: ||dg|| per unit of max_a ||dX_a||. */
+double oracle_mag_local_gauge_bound(const double *X, int nc, double omega, int variant)
+{
+    mat Xm[3];
+    for (int a = 0; a < nc; a++) Xm[a] = get_mat(X, nc, a);
+    bound_track bt = {1.0, 0.0, 0.0, INFINITY};
+    mag_local_gauge_b(Xm, nc, omega, variant, &bt);
+    return bt.dg;
+}
+
 /* the SU(2) maximiser of (1/2) tr[s3 B Z B^+] for a 2x2 hermitian Z */
 void oracle_mag_su2_max(const double *Z, double *B)
 {
@@ -1226,18 +1549,40 @@ void oracle_mag_su2_max(const double *Z, double *B)
  * C = (sqrt(u) cos a, sqrt(w) cos c, sqrt(w) sin c, sqrt(u) sin a) with the
  * angles a = 2 pi v1, c = 2 pi v2 uniform. Counter (site, sweep, sub << 1, 0),
  * one Philox block per subgroup. n = 0 leaves the block alone. */
-static mat mag_heatbath_su2(const mat *Z, double inv_T, const uint32_t *key, uint32_t site, uint32_t sweep, int sub)
+/* u and w = 1 - u of the draw of R16 for the uniform v0 */
+static void mag_hb_uw(double beta, double v0, double *u, double *w)
+{
+    *w = -log1p(v0 * expm1(-beta)) / beta;
+    *u = beta <= 30.0 ? log1p((1.0 - v0) * expm1(beta)) / beta : 1.0 - *w;
+}
+
+static mat mag_heatbath_su2(const mat *Z, double inv_T, const uint32_t *key, uint32_t site, uint32_t sweep, int sub,
+                            bound_track *bt, double rows, double rows_rho)
 {
     double z3 = 0.5 * (Z->m[0][0].re - Z->m[1][1].re);
     double z1 = Z->m[0][1].re, z2 = -Z->m[0][1].im;
     double n = sqrt(z1 * z1 + z2 * z2 + z3 * z3);
-    if (!(n > 0.0)) return mat_identity(2);
+    if (!(n > 0.0)) {
+        if (bt) track_step2(bt, INFINITY, rows, rows_rho);
+        return mat_identity(2);
+    }
     mat Bmax = mag_su2_max(Z);
     double beta = (2.0 * n) * inv_T;
     double v[4];
     draw4(key, site, sweep, (uint32_t)sub << 1, v);
-    double w = -log1p(v[0] * expm1(-beta)) / beta;
-    double u = beta <= 30.0 ? log1p((1.0 - v[0]) * expm1(beta)) / beta : 1.0 - w;
+    double u, w;
+    mag_hb_uw(beta, v[0], &u, &w);
+    if (bt) {
+        /* B = C Bmax: Bmax moves by 2 E / N (mag_max_amp); beta = 2 |z| / T by
+         * at most 4 E / T, and C with it by |dC/dbeta| per unit, C's
+         * components being sqrt(u) and sqrt(w) times fixed unit vectors */
+        double h = FD_STEP * beta, up, wp, um, wm;
+        mag_hb_uw(beta + h, v[0], &up, &wp);
+        mag_hb_uw(beta - h, v[0], &um, &wm);
+        double a = (sqrt(fmax(up, 0.0)) - sqrt(fmax(um, 0.0))) / (2.0 * h);
+        double b = (sqrt(fmax(wp, 0.0)) - sqrt(fmax(wm, 0.0))) / (2.0 * h);
+        track_step2(bt, mag_max_amp(Z) + sqrt(a * a + b * b) * 4.0 * inv_T, rows, rows_rho);
+    }
     double su = sqrt(u), sw = sqrt(w);
     double c[4] = {su * cos(TWO_PI * v[1]), sw * cos(TWO_PI * v[2]), sw * sin(TWO_PI * v[2]), su * sin(TWO_PI * v[1])};
     mat C = quaternion_matrix(c);
@@ -1250,7 +1595,8 @@ static mat mag_heatbath_su2(const mat *Z, double inv_T, const uint32_t *key, uin
 
 /* the MAG heat-bath site transformation: the subgroups of R14 with the draw of
  * R16 in place of the overrelaxed maximiser */
-static mat mag_heatbath_gauge(mat *X, int nc, double inv_T, const uint32_t *key, uint32_t site, uint32_t sweep)
+static mat mag_heatbath_gauge(mat *X, int nc, double inv_T, const uint32_t *key, uint32_t site, uint32_t sweep,
+                              bound_track *bt)
 {
     static const int sub[3][2] = {{0, 1}, {0, 2}, {1, 2}};
     int nsub = nc == 2 ? 1 : 3;
@@ -1263,7 +1609,8 @@ static mat mag_heatbath_gauge(mat *X, int nc, double inv_T, const uint32_t *key,
         Z.m[0][1] = D.m[i][j];
         Z.m[1][0] = D.m[j][i];
         Z.m[1][1] = D.m[j][j];
-        mat r = mag_heatbath_su2(&Z, inv_T, key, site, sweep, s);
+        mat r = mag_heatbath_su2(&Z, inv_T, key, site, sweep, s, bt, bt ? mag_rows(X, nc, i, j, 1) : 0.0,
+                                 bt ? mag_rows(X, nc, i, j, 0) : 0.0);
         mat R = mat_identity(nc);
         R.m[i][i] = r.m[0][0];
         R.m[i][j] = r.m[0][1];
@@ -1279,27 +1626,49 @@ static mat mag_heatbath_gauge(mat *X, int nc, double inv_T, const uint32_t *key,
     return g;
 }
 
+static void mag_heatbath_site_b(double *U, const lattice *lat, int nc, long i, double inv_T, const uint32_t *key,
+                                uint32_t sweep, const bound_ctx *bc)
+{
+    mat X[3];
+    mag_X(U, lat, nc, i, X);
+    bound_track bt;
+    if (bc) bt = track_begin(bc, lat, i, 0, 2.0);
+    mat g = mag_heatbath_gauge(X, nc, inv_T, key, (uint32_t)i, sweep, bc ? &bt : NULL);
+    mat gd = mat_adj(&g);
+    for (int mu = 0; mu < 4; mu++) {
+        long ib = site_shift(lat, i, mu, -1);
+        mat f = get_link(U, nc, i, mu);
+        mat b = get_link(U, nc, ib, mu);
+        mat fn = mat_mul(&g, &f);
+        mat bn = mat_mul(&b, &gd);
+        put_link(U, nc, i, mu, &fn);
+        put_link(U, nc, ib, mu, &bn);
+    }
+    if (bc) track_end(bc, &bt, lat, i, 0);
+}
+
 void oracle_mag_heatbath_halfsweep(double *U, const int *L, int nc, int parity, double T, const uint32_t *key,
                                    uint32_t sweep)
 {
     lattice lat = make_lattice(L);
     double inv_T = 1.0 / T;
 #pragma omp parallel for schedule(static)
-    for (long i = 0; i < lat.V; i++) {
-        if (site_parity(&lat, i, 0) != parity) continue;
-        mat X[3];
-        mag_X(U, &lat, nc, i, X);
-        mat g = mag_heatbath_gauge(X, nc, inv_T, key, (uint32_t)i, sweep);
-        mat gd = mat_adj(&g);
-        for (int mu = 0; mu < 4; mu++) {
-            long ib = site_shift(&lat, i, mu, -1);
-            mat f = get_link(U, nc, i, mu);
-            mat b = get_link(U, nc, ib, mu);
-            mat fn = mat_mul(&g, &f);
-            mat bn = mat_mul(&b, &gd);
-            put_link(U, nc, i, mu, &fn);
-            put_link(U, nc, ib, mu, &bn);
-        }
+    for (long i = 0; i < lat.V; i++)
+        if (site_parity(&lat, i, 0) == parity) mag_heatbath_site_b(U, &lat, nc, i, inv_T, key, sweep, NULL);
+}
+
+/* One MAG heat-bath sweep with the error bounds of oracle_sweep_bound (the
+ * MAG draw takes no decisions, so there is no slack). */
+void oracle_mag_heatbath_sweep_bound(double *U, const int *L, int nc, double T, const uint32_t *key, uint32_t sweep,
+                                     double rho, double *e)
+{
+    lattice lat = make_lattice(L);
+    bound_ctx bc = {e, NULL, rho};
+    double inv_T = 1.0 / T;
+    for (int parity = 0; parity < 2; parity++) {
+#pragma omp parallel for schedule(static)
+        for (long i = 0; i < lat.V; i++)
+            if (site_parity(&lat, i, 0) == parity) mag_heatbath_site_b(U, &lat, nc, i, inv_T, key, sweep, &bc);
     }
 }
 
@@ -1334,7 +1703,7 @@ void oracle_mag_heatbath_su2(const double *Z, double T, const uint32_t *key, uin
                              double *B)
 {
     mat z = get_mat(Z, 2, 0);
-    mat b = mag_heatbath_su2(&z, 1.0 / T, key, site, sweep, sub);
+    mat b = mag_heatbath_su2(&z, 1.0 / T, key, site, sweep, sub, NULL, 0.0, 0.0);
     put_mat(B, 2, 0, &b);
 }
 
@@ -1348,6 +1717,16 @@ void oracle_local_gauge(const double *K, int nc, double omega, int variant, doub
     mat k = get_mat(K, nc, 0);
     mat r = local_gauge(&k, omega, variant);
     put_mat(g, nc, 0, &r);
+}
+
+/* The bound of local_gauge_b for one K: ||dg|| per unit ||dK|| (no rounding
+ * charges), i.e. the site's amplification of an error in its gathered K. */
+double oracle_local_gauge_bound(const double *K, int nc, double omega, int variant)
+{
+    mat k = get_mat(K, nc, 0);
+    bound_track bt = {1.0, 0.0, 0.0, INFINITY};
+    local_gauge_b(&k, omega, variant, &bt);
+    return bt.dg;
 }
 
 /* the SU(2) maximiser of Re tr[r w] for a 2x2 block w (no overrelaxation) */
@@ -1364,8 +1743,21 @@ void oracle_heatbath_gauge(const double *K, int nc, double T, const uint32_t *ke
                            double *g)
 {
     mat k = get_mat(K, nc, 0);
-    mat r = heatbath_gauge(&k, 1.0 / T, key, site, sweep);
+    mat r = heatbath_gauge(&k, 1.0 / T, key, site, sweep, NULL);
     put_mat(g, nc, 0, &r);
+}
+
+/* The bound of the heat-bath site transformation for one K: ||dg|| per unit
+ * ||dK|| with the draws' decisions held (no rounding charges); *slack
+ * receives the smallest decision slack for errors of K up to dK. */
+double oracle_heatbath_gauge_bound(const double *K, int nc, double T, const uint32_t *key, uint32_t site,
+                                   uint32_t sweep, double dK, double *slack)
+{
+    mat k = get_mat(K, nc, 0);
+    bound_track bt = {dK, 0.0, 0.0, INFINITY};
+    heatbath_gauge(&k, 1.0 / T, key, site, sweep, &bt);
+    if (slack) *slack = bt.slack;
+    return bt.dg / dK;
 }
 
 /* g^omega for one SU(2) matrix */
