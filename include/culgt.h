@@ -238,9 +238,11 @@ culgt_status culgt_theta(const void *d_links, const culgt_params *p, void *cuda_
  *            written in stream order (the call does not synchronise).
  * Lattices above 4,194,304 sites return CULGT_ERR_TOO_LARGE before any
  * device work. The first call on a device looks up the array's device
- * address with that device current; make that first call before any stream
- * capture. All calls share the array: calls that overlap on the GPU (other
- * streams, other host threads) race and must be serialised by the caller. */
+ * address with that device current, and so does the first call after the
+ * device's context changed (cudaDeviceReset); make such a call before any
+ * stream capture. All calls share the array: calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller. */
 culgt_status culgt_theta_static_scratch(const void *d_links, const culgt_params *p, void *cuda_stream,
                                         double *d_out);
 

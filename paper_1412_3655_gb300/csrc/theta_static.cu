@@ -33,11 +33,43 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double2 g_theta_scratch[kMaxPartials];
 
-// Device address of g_theta_scratch on each device, looked up once per
-// device with that device current. Host code may not pass the symbol itself
-// to a kernel: on the host it names a stand-in, not device memory.
+// Device address of g_theta_scratch on each device, looked up with that
+// device current. Host code may not pass the symbol itself to a kernel: on the
+// host it names a stand-in, not device memory. The address belongs to the
+// device's current CUDA context; cudaDeviceReset destroys that context and the
+// next one may load the array elsewhere, so the address is cached together
+// with the context's unique id (cuCtxGetId, reached through the runtime's
+// driver entry points, no link to libcuda) and looked up again when the id
+// changes.
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
+
 std::mutex g_setup_mutex;
 double2 *g_scratch_addr[kMaxDevices];
+unsigned long long g_scratch_ctx[kMaxDevices];
+CtxGetCurrentFn g_ctx_get_current;
+CtxGetIdFn g_ctx_get_id;
+
+// id of the calling thread's current context, 0 if none (or not available)
+unsigned long long current_context_id()
+{
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) {
+            (void)cudaGetLastError();
+            return 0;
+        }
+        g_ctx_get_current = (CtxGetCurrentFn)f1;
+        g_ctx_get_id = (CtxGetIdFn)f2;
+    }
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&ctx) != 0 || !ctx || g_ctx_get_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 culgt_status scratch_for_current_device(double2 **out)
 {
@@ -47,13 +79,16 @@ culgt_status scratch_for_current_device(double2 **out)
         return CULGT_ERR_CUDA;
     }
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    unsigned long long id = current_context_id();
+    if (!g_scratch_addr[dev] || id == 0 || id != g_scratch_ctx[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_theta_scratch) != cudaSuccess || !p) {
             (void)cudaGetLastError();
             return CULGT_ERR_CUDA;
         }
         g_scratch_addr[dev] = (double2 *)p;
+        // the lookup makes the device's primary context current if none was
+        g_scratch_ctx[dev] = current_context_id();
     }
     *out = g_scratch_addr[dev];
     return CULGT_OK;
