@@ -106,28 +106,53 @@ template <typename T> __device__ __forceinline__ void m3_identity(M3<T> &a)
     for (int i = 0; i < 3; i++) a.re[i][i] = T(1);
 }
 
-// acc += u
+// acc += u (double-float: without renormalisation, see m3_renorm)
 template <typename T> __device__ __forceinline__ void m3_acc(M3<T> &acc, const M3<T> &u)
 {
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            acc.re[i][j] += u.re[i][j];
-            acc.im[i][j] += u.im[i][j];
+            if constexpr (std::is_same<T, dfl>::value) {
+                acc.re[i][j] = add_lazy(acc.re[i][j], u.re[i][j]);
+                acc.im[i][j] = add_lazy(acc.im[i][j], u.im[i][j]);
+            } else {
+                acc.re[i][j] += u.re[i][j];
+                acc.im[i][j] += u.im[i][j];
+            }
         }
 }
 
-// acc += u^+
+// acc += u^+ (double-float: without renormalisation)
 template <typename T> __device__ __forceinline__ void m3_acc_adj(M3<T> &acc, const M3<T> &u)
 {
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            acc.re[i][j] += u.re[j][i];
-            acc.im[i][j] -= u.im[j][i];
+            if constexpr (std::is_same<T, dfl>::value) {
+                acc.re[i][j] = add_lazy(acc.re[i][j], u.re[j][i]);
+                acc.im[i][j] = add_lazy(acc.im[i][j], -u.im[j][i]);
+            } else {
+                acc.re[i][j] += u.re[j][i];
+                acc.im[i][j] -= u.im[j][i];
+            }
         }
+}
+
+// a sum of m3_acc / m3_acc_adj terms back to normalised pairs (no-op
+// except for double-float)
+template <typename T> __device__ __forceinline__ void m3_renorm(M3<T> &a)
+{
+    if constexpr (std::is_same<T, dfl>::value) {
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                a.re[i][j] = dfl_renorm(a.re[i][j]);
+                a.im[i][j] = dfl_renorm(a.im[i][j]);
+            }
+    }
 }
 
 // Complex 3x3 products written as explicit fused multiply-add chains: one
@@ -138,6 +163,29 @@ template <typename T> __device__ __forceinline__ void m3_acc_adj(M3<T> &acc, con
 template <int R0, int R1, typename T>
 __device__ __forceinline__ void m3_mul_rows(M3<T> &c, const M3<T> &a, const M3<T> &b)
 {
+    if constexpr (std::is_same<T, dfl>::value) {
+        // double-float: each real output one compensated sum of six products
+#pragma unroll
+        for (int i = R0; i <= R1; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                dfacc sr = dfacc_mul(a.re[i][0], b.re[0][j]);
+                dfacc_fma(sr, -a.im[i][0], b.im[0][j]);
+                dfacc_fma(sr, a.re[i][1], b.re[1][j]);
+                dfacc_fma(sr, -a.im[i][1], b.im[1][j]);
+                dfacc_fma(sr, a.re[i][2], b.re[2][j]);
+                dfacc_fma(sr, -a.im[i][2], b.im[2][j]);
+                dfacc si = dfacc_mul(a.re[i][0], b.im[0][j]);
+                dfacc_fma(si, a.im[i][0], b.re[0][j]);
+                dfacc_fma(si, a.re[i][1], b.im[1][j]);
+                dfacc_fma(si, a.im[i][1], b.re[1][j]);
+                dfacc_fma(si, a.re[i][2], b.im[2][j]);
+                dfacc_fma(si, a.im[i][2], b.re[2][j]);
+                c.re[i][j] = dfacc_get(sr);
+                c.im[i][j] = dfacc_get(si);
+            }
+        return;
+    }
 #pragma unroll
     for (int i = R0; i <= R1; i++)
 #pragma unroll
@@ -163,6 +211,28 @@ __device__ __forceinline__ void m3_mul_rows(M3<T> &c, const M3<T> &a, const M3<T
 template <int R0, int R1, typename T>
 __device__ __forceinline__ void m3_mul_adj_rows(M3<T> &c, const M3<T> &a, const M3<T> &b)
 {
+    if constexpr (std::is_same<T, dfl>::value) {
+#pragma unroll
+        for (int i = R0; i <= R1; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                dfacc sr = dfacc_mul(a.re[i][0], b.re[j][0]);
+                dfacc_fma(sr, a.im[i][0], b.im[j][0]);
+                dfacc_fma(sr, a.re[i][1], b.re[j][1]);
+                dfacc_fma(sr, a.im[i][1], b.im[j][1]);
+                dfacc_fma(sr, a.re[i][2], b.re[j][2]);
+                dfacc_fma(sr, a.im[i][2], b.im[j][2]);
+                dfacc si = dfacc_mul(a.im[i][0], b.re[j][0]);
+                dfacc_fma(si, -a.re[i][0], b.im[j][0]);
+                dfacc_fma(si, a.im[i][1], b.re[j][1]);
+                dfacc_fma(si, -a.re[i][1], b.im[j][1]);
+                dfacc_fma(si, a.im[i][2], b.re[j][2]);
+                dfacc_fma(si, -a.re[i][2], b.im[j][2]);
+                c.re[i][j] = dfacc_get(sr);
+                c.im[i][j] = dfacc_get(si);
+            }
+        return;
+    }
 #pragma unroll
     for (int i = R0; i <= R1; i++)
 #pragma unroll
@@ -200,6 +270,23 @@ template <typename T> __device__ __forceinline__ void m3_mul_adj(M3<T> &c, const
 // first two (the 12-parameter reconstruction, Sec. 3.1)
 template <typename T> __device__ __forceinline__ void m3_rebuild_row2(M3<T> &u)
 {
+    if constexpr (std::is_same<T, dfl>::value) {
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            const int c = (b + 1) % 3, d = (b + 2) % 3;
+            dfacc xr = dfacc_mul(u.re[0][c], u.re[1][d]);
+            dfacc_fma(xr, -u.im[0][c], u.im[1][d]);
+            dfacc_fma(xr, -u.re[0][d], u.re[1][c]);
+            dfacc_fma(xr, u.im[0][d], u.im[1][c]);
+            dfacc xi = dfacc_mul(u.re[0][c], u.im[1][d]);
+            dfacc_fma(xi, u.im[0][c], u.re[1][d]);
+            dfacc_fma(xi, -u.re[0][d], u.im[1][c]);
+            dfacc_fma(xi, -u.im[0][d], u.re[1][c]);
+            u.re[2][b] = dfacc_get(xr);
+            u.im[2][b] = -dfacc_get(xi);
+        }
+        return;
+    }
 #pragma unroll
     for (int b = 0; b < 3; b++) {
         const int c = (b + 1) % 3, d = (b + 2) % 3;
@@ -290,10 +377,36 @@ template <typename T> __device__ __forceinline__ Q4<T> q_mul_adj(const Q4<T> &a,
 // beta = omega (1 + (omega-1)(c0-1)), rescaled to unit length.
 // variant 1: the exact power (cos(omega phi), c/|c| sin(omega phi)).
 // |a| = 0 leaves the block alone (q = 1).
+// a^2 + b^2 + c^2 + d^2 (double-float: one compensated sum)
+template <typename T> __device__ __forceinline__ T sumsq4(T a, T b, T c, T d)
+{
+    if constexpr (std::is_same<T, dfl>::value) {
+        dfacc s = dfacc_mul(a, a);
+        dfacc_fma(s, b, b);
+        dfacc_fma(s, c, c);
+        dfacc_fma(s, d, d);
+        return dfacc_get(s);
+    } else {
+        return a * a + b * b + c * c + d * d;
+    }
+}
+
+// a b + c d as fma(a, b, c d) (double-float: one compensated sum)
+template <typename T> __device__ __forceinline__ T mul_add2(T a, T b, T c, T d)
+{
+    if constexpr (std::is_same<T, dfl>::value) {
+        dfacc s = dfacc_mul(c, d);
+        dfacc_fma(s, a, b);
+        return dfacc_get(s);
+    } else {
+        return fma(a, b, c * d);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void su2_or_step(T a0, T a1, T a2, T a3, T omega, int variant, T q[4])
 {
-    T n2 = a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3;
+    T n2 = sumsq4(a0, a1, a2, a3);
     if (!(n2 > T(0))) {
         q[0] = T(1);
         q[1] = q[2] = q[3] = T(0);
@@ -305,7 +418,7 @@ __device__ __forceinline__ void su2_or_step(T a0, T a1, T a2, T a3, T omega, int
         T beta = omega * (T(1) + (omega - T(1)) * (c0 - T(1)));
         T x0 = (T(1) - omega) + beta * c0;
         T x1 = beta * c1, x2 = beta * c2, x3 = beta * c3;
-        T m = rsqrt(x0 * x0 + x1 * x1 + x2 * x2 + x3 * x3);
+        T m = rsqrt(sumsq4(x0, x1, x2, x3));
         q[0] = x0 * m;
         q[1] = x1 * m;
         q[2] = x2 * m;
@@ -331,6 +444,33 @@ __device__ __forceinline__ void su2_or_step(T a0, T a1, T a2, T a3, T omega, int
 // rows i, j of m  <-  R rows, R = [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]]
 template <typename T, int I, int J> __device__ __forceinline__ void rotate_rows(M3<T> &m, const T q[4])
 {
+    if constexpr (std::is_same<T, dfl>::value) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const dfl xr = m.re[I][c], xi = m.im[I][c], yr = m.re[J][c], yi = m.im[J][c];
+            dfacc a = dfacc_mul(q[0], xr);
+            dfacc_fma(a, -q[3], xi);
+            dfacc_fma(a, q[2], yr);
+            dfacc_fma(a, -q[1], yi);
+            dfacc b = dfacc_mul(q[0], xi);
+            dfacc_fma(b, q[3], xr);
+            dfacc_fma(b, q[2], yi);
+            dfacc_fma(b, q[1], yr);
+            dfacc e = dfacc_mul(q[0], yr);
+            dfacc_fma(e, q[3], yi);
+            dfacc_fma(e, -q[2], xr);
+            dfacc_fma(e, -q[1], xi);
+            dfacc f = dfacc_mul(q[0], yi);
+            dfacc_fma(f, -q[3], yr);
+            dfacc_fma(f, -q[2], xi);
+            dfacc_fma(f, q[1], xr);
+            m.re[I][c] = dfacc_get(a);
+            m.im[I][c] = dfacc_get(b);
+            m.re[J][c] = dfacc_get(e);
+            m.im[J][c] = dfacc_get(f);
+        }
+        return;
+    }
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         T xr = m.re[I][c], xi = m.im[I][c], yr = m.re[J][c], yi = m.im[J][c];
@@ -409,10 +549,10 @@ __device__ __forceinline__ void su3_local_gauge_step(M3<T> &K, M3<T> &g, const S
 #pragma unroll
     for (int c = 0; c < 2; c++) {
         T xr = g.re[0][c], xi = g.im[0][c];
-        g.re[0][c] = fma(-q[3], xi, q[0] * xr);
-        g.im[0][c] = fma(q[3], xr, q[0] * xi);
-        g.re[2][c] = fma(-q[1], xi, -q[2] * xr);
-        g.im[2][c] = fma(q[1], xr, -q[2] * xi);
+        g.re[0][c] = mul_add2(-q[3], xi, q[0], xr);
+        g.im[0][c] = mul_add2(q[3], xr, q[0], xi);
+        g.re[2][c] = mul_add2(-q[1], xi, -q[2], xr);
+        g.im[2][c] = mul_add2(q[1], xr, -q[2], xi);
     }
     g.re[0][2] = q[2];
     g.im[0][2] = q[1];

@@ -123,6 +123,68 @@ __device__ __forceinline__ dfl operator/(dfl a, dfl b)
     return a * inv;
 }
 
+// Sums of products with a single renormalisation at the end (the compensated
+// dot product of Ogita, Rump and Oishi, "Accurate sum and dot product", 2005,
+// for double-float factors): s collects the leading products hi*hi by
+// Knuth's two-sum, e every exact product error (FMA), both cross products
+// hi*lo and lo*hi and every two-sum error. e stays about 2^-24 of the terms,
+// so its own float rounding is about 2^-48 of them, like one double-float
+// operation per term; lo*lo products (2^-48 of a term) are dropped as in
+// operator*. Twelve float operations a term against fifteen for a chain of
+// double-float fma, and one renormalisation per sum instead of one per term.
+struct dfacc {
+    float s, e;
+};
+
+// acc = a b
+__device__ __forceinline__ dfacc dfacc_mul(dfl a, dfl b)
+{
+    dfacc r;
+    r.s = a.hi * b.hi;
+    r.e = fmaf(a.hi, b.hi, -r.s);
+    r.e = fmaf(a.hi, b.lo, r.e);
+    r.e = fmaf(a.lo, b.hi, r.e);
+    return r;
+}
+
+// acc += a b
+__device__ __forceinline__ void dfacc_fma(dfacc &r, dfl a, dfl b)
+{
+    const float p = a.hi * b.hi;
+    float q = fmaf(a.hi, b.hi, -p);
+    q = fmaf(a.hi, b.lo, q);
+    q = fmaf(a.lo, b.hi, q);
+    float s, t;
+    two_sum(r.s, p, s, t);
+    r.s = s;
+    r.e += t + q;
+}
+
+__device__ __forceinline__ dfl dfacc_get(const dfacc &r)
+{
+    dfl o;
+    fast_two_sum(r.s, r.e, o.hi, o.lo);
+    return o;
+}
+
+// a + b without the final renormalisation, for long runs of additions (the
+// gathered K): hi is the exact two-sum of the high parts, lo collects its
+// error and both low parts (a few ulp(hi) after many additions);
+// dfl_renorm restores |lo| <= ulp(hi) / 2 once at the end
+__device__ __forceinline__ dfl add_lazy(dfl a, dfl b)
+{
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return dfl(s, e + (a.lo + b.lo));
+}
+
+__device__ __forceinline__ dfl dfl_renorm(dfl a)
+{
+    dfl r;
+    fast_two_sum(a.hi, a.lo, r.hi, r.lo);
+    return r;
+}
+
 // transcendental functions only appear in the exact-power overrelaxation
 // variant; they go through double
 __device__ __forceinline__ dfl atan2(dfl y, dfl x) { return dfl(::atan2((double)y, (double)x)); }

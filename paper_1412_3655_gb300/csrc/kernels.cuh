@@ -94,10 +94,25 @@ __device__ __forceinline__ void su3_update(typename P::Chunk *base, const Geom &
         m3_acc(Kt, f);
         m3_acc_adj(Kt, b);
     }
+    // double-float: each half was summed without renormalising (m3_acc);
+    // it is renormalised before the halves are added, so that one thread and
+    // a pair of threads per site form the same K
+    m3_renorm(Ka);
     M3<T> K;
     if constexpr (TPS == 1) {
+        m3_renorm(Kb);
         K = Ka;
-        m3_acc(K, Kb);
+        if constexpr (std::is_same<T, dfl>::value) {
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    K.re[i][j] = Ka.re[i][j] + Kb.re[i][j];
+                    K.im[i][j] = Ka.im[i][j] + Kb.im[i][j];
+                }
+        } else {
+            m3_acc(K, Kb);
+        }
     } else {
         // the partner's partial; both lanes then add half 0 + half 1
 #pragma unroll
