@@ -150,21 +150,28 @@ __device__ __forceinline__ uint32_t canonical_site(const Geom &g, int cb, int p)
     return (uint32_t)(x[1] + g.L[1] * (x[2] + g.L[2] * (x[3] + g.L[3] * x[0])));
 }
 
-// One heat-bath half-sweep of parity `parity` at 1/T = inv_temp, one thread
-// per site in blocks of 128; acc: also gacc(x) <- g(x) gacc(x) (FP32 phase
-// of the mixed schedule). KEEP: hold the eight links in registers between the
-// gather and the update (SU(3)); MINB: blocks per SM the registers are capped
-// for. Both only trade registers against re-reads and occupancy: the links
-// come out bitwise the same.
+// alpha_scale of HbStep for 1/T = inv_temp, in the links' arithmetic type
+// (rounded once, on the host)
+template <class P> inline typename P::Real hb_alpha_scale(double inv_temp)
+{
+    return (typename P::Real)(P::NC == 3 ? inv_temp : 2.0 * inv_temp);
+}
+
+// One heat-bath half-sweep of parity `parity`, one thread per site in blocks
+// of 128, alpha_scale = hb_alpha_scale<P>(1/T); acc: also gacc(x) <- g(x)
+// gacc(x) (FP32 phase of the mixed schedule). KEEP: hold the eight links in
+// registers between the gather and the update (SU(3)); MINB: blocks per SM the
+// registers are capped for. Both only trade registers against re-reads and
+// occupancy: the links come out bitwise the same.
 template <class P, class PG, bool KEEP, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_heatbath(typename P::Chunk *base, typename PG::Chunk *gacc, Geom g,
-                                                        int parity, double inv_temp, uint32_t k0, uint32_t k1,
-                                                        uint32_t sweep, int acc)
+                                                        int parity, typename P::Real alpha_scale, uint32_t k0,
+                                                        uint32_t k1, uint32_t sweep, int acc)
 {
     typedef typename P::Real T;
     const int cb = blockIdx.x * blockDim.x + threadIdx.x;
     if (cb >= g.Vh) return;
-    const HbStep<T> step{(T)(P::NC == 3 ? inv_temp : 2.0 * inv_temp), k0, k1, canonical_site(g, cb, parity), sweep};
+    const HbStep<T> step{alpha_scale, k0, k1, canonical_site(g, cb, parity), sweep};
     if constexpr (P::NC == 3) {
         M3<T> G;
         su3_update<P, KEEP, 1>(base, g, cb, parity, 0, true, 0, step, &G);

@@ -47,6 +47,7 @@ struct BRule {
     double fp32_target;  // theta at which the FP32 phase ends (switch_theta if mixed, else theta_target)
     int fp32_next;       // PH_SWITCH (mixed) or PH_DONE (FP32 only)
     int max_sweeps;
+    int auto_switch;     // mixed with switch_theta = 0: also end the FP32 phase when theta stalls
 };
 
 // gacc(x) <- g(x) gacc(x) for a problem's site (cb, p) in PG's storage
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(kSweepTile) k_b_mag_halfsweep(const BProb *pro
 // one colour of a MAG heat-bath half-sweep; problem j draws with seed + j
 template <class P, class PG>
 __global__ void __launch_bounds__(kSweepTile) k_b_mag_heatbath(const BProb *probs, const int *tile_prob, int colour,
-                                                              int want_phase, double inv_temp,
+                                                              int want_phase, typename P::Real two_inv_temp,
                                                               unsigned long long seed, uint32_t sweep)
 {
     typedef typename P::Real T;
@@ -142,8 +143,7 @@ __global__ void __launch_bounds__(kSweepTile) k_b_mag_heatbath(const BProb *prob
     const int cb = pr.cb_begin + local;
     const int p = (colour + pr.par_off) & 1;
     const unsigned long long key = seed + (unsigned long long)j;
-    const MagHbStep<T> step{(T)(2.0 * inv_temp), (uint32_t)key, (uint32_t)(key >> 32), canonical_site(pr.g, cb, p),
-                            sweep};
+    const MagHbStep<T> step{two_inv_temp, (uint32_t)key, (uint32_t)(key >> 32), canonical_site(pr.g, cb, p), sweep};
     b_mag_site_update<P, PG>(pr, cb, p, want_phase, step);
 }
 
@@ -174,12 +174,14 @@ template <class P> struct BHb {
     static constexpr int minb = (kFP32 && P::NC == 3) ? 4 : 1;
 };
 
-// One colour of a heat-bath half-sweep (simulated annealing) at 1/T =
-// inv_temp over every problem in want_phase. Problem j draws with the key
-// seed + j, so its draws are those of a single-lattice call with that seed.
+// One colour of a heat-bath half-sweep (simulated annealing) over every
+// problem in want_phase, alpha_scale = hb_alpha_scale<P>(1/T). Problem j draws
+// with the key seed + j, so its draws are those of a single-lattice call with
+// that seed.
 template <class P, class PG>
 __global__ void __launch_bounds__(kSweepTile, BHb<P>::minb) k_b_heatbath(const BProb *probs, const int *tile_prob,
-                                                                        int colour, int want_phase, double inv_temp,
+                                                                        int colour, int want_phase,
+                                                                        typename P::Real alpha_scale,
                                                                         unsigned long long seed, uint32_t sweep)
 {
     typedef typename P::Real T;
@@ -192,8 +194,7 @@ __global__ void __launch_bounds__(kSweepTile, BHb<P>::minb) k_b_heatbath(const B
     const int cb = pr.cb_begin + local;
     const int p = (colour + pr.par_off) & 1;
     const unsigned long long key = seed + (unsigned long long)j;
-    const HbStep<T> step{(T)(P::NC == 3 ? inv_temp : 2.0 * inv_temp), (uint32_t)key, (uint32_t)(key >> 32),
-                         canonical_site(pr.g, cb, p), sweep};
+    const HbStep<T> step{alpha_scale, (uint32_t)key, (uint32_t)(key >> 32), canonical_site(pr.g, cb, p), sweep};
     b_site_update<P, PG, BHb<P>::keep>(pr, cb, p, want_phase, step);
 }
 

@@ -97,10 +97,11 @@ template <class P> struct BImpl {
     static void heatbath(const BProb *probs, const int *map, int ntiles, int colour, int phase, double inv_temp,
                          unsigned long long seed, uint32_t sweep, bool acc, cudaStream_t s)
     {
+        const typename P::Real as = hb_alpha_scale<P>(inv_temp);
         if (acc)
-            k_b_heatbath<P, PG><<<ntiles, kSweepTile, 0, s>>>(probs, map, colour, phase, inv_temp, seed, sweep);
+            k_b_heatbath<P, PG><<<ntiles, kSweepTile, 0, s>>>(probs, map, colour, phase, as, seed, sweep);
         else
-            k_b_heatbath<P, void><<<ntiles, kSweepTile, 0, s>>>(probs, map, colour, phase, inv_temp, seed, sweep);
+            k_b_heatbath<P, void><<<ntiles, kSweepTile, 0, s>>>(probs, map, colour, phase, as, seed, sweep);
         count_launch();
     }
     static void mag_sweep(const BProb *probs, const int *map, int ntiles, int colour, int phase, double omega,
@@ -115,10 +116,11 @@ template <class P> struct BImpl {
     static void mag_heatbath(const BProb *probs, const int *map, int ntiles, int colour, int phase, double inv_temp,
                              unsigned long long seed, uint32_t sweep, bool acc, cudaStream_t s)
     {
+        const typename P::Real t2 = (typename P::Real)(2.0 * inv_temp);
         if (acc)
-            k_b_mag_heatbath<P, PG><<<ntiles, kSweepTile, 0, s>>>(probs, map, colour, phase, inv_temp, seed, sweep);
+            k_b_mag_heatbath<P, PG><<<ntiles, kSweepTile, 0, s>>>(probs, map, colour, phase, t2, seed, sweep);
         else
-            k_b_mag_heatbath<P, void><<<ntiles, kSweepTile, 0, s>>>(probs, map, colour, phase, inv_temp, seed, sweep);
+            k_b_mag_heatbath<P, void><<<ntiles, kSweepTile, 0, s>>>(probs, map, colour, phase, t2, seed, sweep);
         count_launch();
     }
     static void mag_theta(const BProb *probs, const int *map, int ntiles, int phase, int only_switched,

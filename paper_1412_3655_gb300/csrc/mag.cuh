@@ -315,13 +315,13 @@ __global__ void __launch_bounds__(128) k_mag_halfsweep(typename P::Chunk *base, 
 // keyed by (k0, k1) with the canonical site index and sweep word
 template <class P, class PG>
 __global__ void __launch_bounds__(128) k_mag_heatbath(typename P::Chunk *base, typename PG::Chunk *gacc, Geom g,
-                                                      int parity, double inv_temp, uint32_t k0, uint32_t k1,
-                                                      uint32_t sweep, int acc)
+                                                      int parity, typename P::Real two_inv_temp, uint32_t k0,
+                                                      uint32_t k1, uint32_t sweep, int acc)
 {
     typedef typename P::Real T;
     const int cb = blockIdx.x * blockDim.x + threadIdx.x;
     if (cb >= g.Vh) return;
-    const MagHbStep<T> step{(T)(2.0 * inv_temp), k0, k1, canonical_site(g, cb, parity), sweep};
+    const MagHbStep<T> step{two_inv_temp, k0, k1, canonical_site(g, cb, parity), sweep};
     typename P::Link G;
     mag_site_update<P>(base, g, cb, parity, step, &G);
     if (acc) accumulate_gauge<P, PG>(gacc, g, parity, cb, G);

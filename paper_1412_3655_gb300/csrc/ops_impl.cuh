@@ -55,21 +55,22 @@ template <class P> struct OpsImpl {
         C *b = (C *)base;
         GC *a = (GC *)gacc;
         constexpr bool K0 = KeepLinks<P>::value;
+        const typename P::Real as = hb_alpha_scale<P>(inv_temp);
         if constexpr (HbMappings<P>::count == 5) {
             switch (variant) {
-            case 1: k_heatbath<P, PG, true, 3><<<nb, 128, 0, s>>>(b, a, g, parity, inv_temp, k0, k1, sweep, acc); break;
-            case 2: k_heatbath<P, PG, false, 1><<<nb, 128, 0, s>>>(b, a, g, parity, inv_temp, k0, k1, sweep, acc); break;
-            case 3: k_heatbath<P, PG, false, 3><<<nb, 128, 0, s>>>(b, a, g, parity, inv_temp, k0, k1, sweep, acc); break;
-            case 4: k_heatbath<P, PG, false, 4><<<nb, 128, 0, s>>>(b, a, g, parity, inv_temp, k0, k1, sweep, acc); break;
-            default: k_heatbath<P, PG, true, 1><<<nb, 128, 0, s>>>(b, a, g, parity, inv_temp, k0, k1, sweep, acc);
+            case 1: k_heatbath<P, PG, true, 3><<<nb, 128, 0, s>>>(b, a, g, parity, as, k0, k1, sweep, acc); break;
+            case 2: k_heatbath<P, PG, false, 1><<<nb, 128, 0, s>>>(b, a, g, parity, as, k0, k1, sweep, acc); break;
+            case 3: k_heatbath<P, PG, false, 3><<<nb, 128, 0, s>>>(b, a, g, parity, as, k0, k1, sweep, acc); break;
+            case 4: k_heatbath<P, PG, false, 4><<<nb, 128, 0, s>>>(b, a, g, parity, as, k0, k1, sweep, acc); break;
+            default: k_heatbath<P, PG, true, 1><<<nb, 128, 0, s>>>(b, a, g, parity, as, k0, k1, sweep, acc);
             }
         } else if constexpr (HbMappings<P>::count == 2) {
             if (variant == 1)
-                k_heatbath<P, PG, K0, 4><<<nb, 128, 0, s>>>(b, a, g, parity, inv_temp, k0, k1, sweep, acc);
+                k_heatbath<P, PG, K0, 4><<<nb, 128, 0, s>>>(b, a, g, parity, as, k0, k1, sweep, acc);
             else
-                k_heatbath<P, PG, K0, 1><<<nb, 128, 0, s>>>(b, a, g, parity, inv_temp, k0, k1, sweep, acc);
+                k_heatbath<P, PG, K0, 1><<<nb, 128, 0, s>>>(b, a, g, parity, as, k0, k1, sweep, acc);
         } else {
-            k_heatbath<P, PG, K0, 1><<<nb, 128, 0, s>>>(b, a, g, parity, inv_temp, k0, k1, sweep, acc);
+            k_heatbath<P, PG, K0, 1><<<nb, 128, 0, s>>>(b, a, g, parity, as, k0, k1, sweep, acc);
         }
         count_launch();
     }
@@ -92,7 +93,8 @@ template <class P> struct OpsImpl {
     {
         typedef typename GaugeParam<P>::type PG;
         k_mag_heatbath<P, PG><<<blocks_for(g.Vh, 128), 128, 0, s>>>((C *)base, (typename PG::Chunk *)gacc, g, parity,
-                                                                     inv_temp, k0, k1, sweep, gacc != nullptr);
+                                                                     (typename P::Real)(2.0 * inv_temp), k0, k1, sweep,
+                                                                     gacc != nullptr);
         count_launch();
     }
     static int mag_theta_partials(const void *base, const Geom &g, double2 *partials, cudaStream_t s)
