@@ -100,7 +100,9 @@ typedef struct {
     int max_sweeps;      /* total sweep budget (both phases of the mixed schedule) */
     int check_every;     /* theta is measured before the first sweep and every check_every sweeps */
     int reunit_every;    /* reunitarise after sweep n when n % reunit_every == 0; 0 = never */
-    double switch_theta; /* mixed: leave the FP32 phase once theta < switch_theta */
+    double switch_theta; /* mixed: leave the FP32 phase once theta < switch_theta; 0 = automatic:
+                            past 1e-8 for as long as every check interval still lowers theta,
+                            switching at the first that does not (the FP32 rounding floor) */
     int dtype_in;        /* canonical link buffer element type: 0 = double, 1 = float */
     int threads_per_site; /* half-sweep mapping: 1 or 2 threads per site; 0 = autotune */
     int block_size;       /* half-sweep threads per block: 64, 128 or 256; 0 = autotune */

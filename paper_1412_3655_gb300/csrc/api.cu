@@ -102,7 +102,8 @@ culgt_status validate(const culgt_params *p)
     if (p->nc == 2 && p->storage_reals != 0 && p->storage_reals != 4) return CULGT_ERR_NC;
     if (!(p->theta_target >= 0.0) || std::isinf(p->theta_target)) return CULGT_ERR_ARG;
     if (p->max_sweeps < 0 || p->check_every < 1 || p->reunit_every < 0) return CULGT_ERR_ARG;
-    if ((p->precision == CULGT_MIXED || p->precision == CULGT_MIXED_DF) && !(p->switch_theta > 0.0))
+    if ((p->precision == CULGT_MIXED || p->precision == CULGT_MIXED_DF) &&
+        !(p->switch_theta > 0.0 || p->switch_theta == 0.0))
         return CULGT_ERR_ARG;
     if (p->dtype_in != 0 && p->dtype_in != 1) return CULGT_ERR_ARG;
     if (p->threads_per_site < 0 || p->threads_per_site > 2) return CULGT_ERR_ARG;
@@ -574,11 +575,17 @@ culgt_status run_interval(culgt_handle *h, int k, int n)
 // Sweeps the current links until theta < target or the running total n
 // reaches max_sweeps; theta is measured first and every check_every sweeps.
 // Each check interval is one CUDA graph replay and one host read of theta.
-culgt_status run_phase(culgt_handle *h, double target, int *n, int *phase_sweeps, double *theta, double *F)
+// until_stall (the automatic switch): also stop at the first check, once
+// theta < kAutoSwitchFloor, that did not lower theta.
+culgt_status run_phase(culgt_handle *h, double target, int *n, int *phase_sweeps, double *theta, double *F,
+                       bool until_stall = false)
 {
     const culgt_params &p = h->prm;
     ST(theta_now(h, theta, F));
+    double prev = INFINITY;
     while (!(*theta < target) && *n < p.max_sweeps) {
+        if (until_stall && *theta < kAutoSwitchFloor && !(*theta < prev)) break;
+        prev = *theta;
         int k = p.check_every;
         if (k > p.max_sweeps - *n) k = p.max_sweeps - *n;
         ST(run_interval(h, k, *n));
@@ -601,7 +608,10 @@ culgt_status fix_handle(culgt_handle *h, culgt_result *out)
     int n = 0;
     h->sweeps32 = h->sweeps64 = 0;
     if ((p.precision == CULGT_MIXED || p.precision == CULGT_MIXED_DF) && h->cur32) {
-        ST(run_phase(h, p.switch_theta, &n, &h->sweeps32, &theta, &F));
+        if (p.switch_theta > 0.0)
+            ST(run_phase(h, p.switch_theta, &n, &h->sweeps32, &theta, &F));
+        else
+            ST(run_phase(h, p.theta_target, &n, &h->sweeps32, &theta, &F, true));
         ST(culgt_handle_to_fp64(h));
     }
     ST(run_phase(h, p.theta_target, &n, h->cur32 ? &h->sweeps32 : &h->sweeps64, &theta, &F));

@@ -103,7 +103,8 @@ struct Engine {
         acc32 = has32 && (has64 || coulomb || want_gauge);
         acc64 = has64 && (coulomb || want_gauge);
         rule.theta_target = p->theta_target;
-        rule.fp32_target = mixed ? p->switch_theta : p->theta_target;
+        rule.auto_switch = mixed && p->switch_theta == 0.0;
+        rule.fp32_target = (mixed && !rule.auto_switch) ? p->switch_theta : p->theta_target;
         rule.fp32_next = mixed ? PH_SWITCH : PH_DONE;
         rule.max_sweeps = p->max_sweeps;
         if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {

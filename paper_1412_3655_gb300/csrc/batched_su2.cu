@@ -55,6 +55,8 @@ __global__ void k_b_decide(BProb *probs, const double2 *partials, int want_phase
         b += __shfl_down_sync(0xffffffffu, b, o);
     }
     if (threadIdx.x != 0) return;
+    // theta at the problem's previous check (none before its first)
+    const double prev = (pr.sweeps32 + pr.sweeps64 == 0 && want_phase == PH_FP32) ? INFINITY : pr.theta;
     if (want_phase == PH_FP32)
         pr.sweeps32 += k_sweeps;
     else
@@ -66,9 +68,14 @@ __global__ void k_b_decide(BProb *probs, const double2 *partials, int want_phase
     if (!isfinite(pr.theta) || !isfinite(pr.F)) {
         pr.phase = PH_NONFINITE;
     } else if (want_phase == PH_FP32) {
-        // the mixed schedule switches at max_sweeps too, so that every result ends in FP64
-        if (pr.theta < rule.fp32_target || n >= rule.max_sweeps)
-            pr.phase = pr.theta < rule.fp32_target ? rule.fp32_next : (rule.fp32_next == PH_SWITCH ? PH_SWITCH : PH_MAXED);
+        // the mixed schedule switches at max_sweeps too, so that every result
+        // ends in FP64; the automatic switch also when theta stalls below
+        // kAutoSwitchFloor (the FP32 rounding floor)
+        const bool stalled = rule.auto_switch && pr.theta < kAutoSwitchFloor && !(pr.theta < prev);
+        if (pr.theta < rule.fp32_target || stalled || n >= rule.max_sweeps)
+            pr.phase = (pr.theta < rule.fp32_target || stalled)
+                           ? rule.fp32_next
+                           : (rule.fp32_next == PH_SWITCH ? PH_SWITCH : PH_MAXED);
     } else {
         if (pr.theta < rule.theta_target)
             pr.phase = PH_DONE;

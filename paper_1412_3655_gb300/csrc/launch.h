@@ -8,6 +8,11 @@
 
 namespace culgt {
 
+// switch_theta = 0 (automatic switch of the mixed schedules): the FP32 phase
+// goes past this theta for as long as every check interval still lowers
+// theta, and switches at the first that does not (the FP32 rounding floor)
+constexpr double kAutoSwitchFloor = 1e-8;
+
 // geometry of an L0 x L1 x L2 x L3 lattice in the internal layout
 inline Geom make_geom(const int *dims)
 {

@@ -26,6 +26,8 @@ ERR_ARG, ERR_DIMS, ERR_NC, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_TIMEOUT = -1, -
 ERR_TOO_LARGE = -8
 FP64, FP32, MIXED, MIXED_DF, DF = 0, 1, 2, 3, 4
 LANDAU, MAG = 0, 1
+# switch_theta of the automatic FP32 -> FP64 switch of the mixed schedules
+SWITCH_AUTO = 0.0
 
 
 class CulgtError(RuntimeError):

@@ -60,7 +60,8 @@ def test_defaults_validate(lib):
     ({"check_every": 0}, -1),
     ({"max_sweeps": -1}, -1),
     ({"precision": 5}, -1),
-    ({"precision": 2, "switch_theta": 0.0}, -1),
+    ({"precision": 2, "switch_theta": float("nan")}, -1),
+    ({"precision": 2, "switch_theta": -1e-8}, -1),
     ({"precision": 3, "switch_theta": -1.0}, -1),
     ({"theta_target": float("inf")}, -1),
     ({"dtype_in": 2}, -1),
@@ -77,6 +78,13 @@ def test_validate_rejects(lib, change, code):
     # the one-call entry points check before touching the device
     so = lib.library()
     assert so.culgt_landau_fix(ctypes.c_void_p(16), ctypes.byref(p._c()), None, None) == code
+
+
+@pytest.mark.parametrize("precision", [2, 3])
+def test_automatic_switch_validates(lib, precision):
+    """switch_theta = 0 selects the automatic switch of the mixed schedules."""
+    p = lib.Params.defaults(3, (4, 4, 4, 4), precision=precision, switch_theta=0.0)
+    assert lib.culgt_validate(p) == lib.OK
 
 
 @pytest.mark.parametrize("precision", [0, 1, 2, 3, 4])

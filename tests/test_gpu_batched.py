@@ -137,6 +137,22 @@ def test_batched_single_problem_matches_handle(cu, nc, precision):
     assert torch.allclose(a, b, atol=1e-12, rtol=0)
 
 
+@pytest.mark.parametrize("nc", [2, 3])
+def test_batched_automatic_switch_matches_handle(cu, nc):
+    """The batched engine takes the automatic switch on the device per
+    problem, at the same check as the single-lattice handle."""
+    dims = (4, 4, 4, 4)
+    Us = [synth.gauge_config(dims, nc, 0.3, s) for s in (1, 2)]
+    p = cu.Params.defaults(nc, dims, precision=cu.MIXED, check_every=5, reunit_every=50, switch_theta=0.0,
+                           max_sweeps=6000)
+    res = cu.culgt_fix_batched([to_dev(U) for U in Us], [dims, dims], p)
+    for U, rb in zip(Us, res):
+        ra = cu.culgt_landau_fix(to_dev(U), p)
+        assert rb.status == cu.OK
+        assert (ra.sweeps_fp32, ra.sweeps_fp64) == (rb.sweeps_fp32, rb.sweeps_fp64)
+        assert ra.F == pytest.approx(rb.F, rel=1e-12)
+
+
 def test_batched_max_sweeps_and_status(cu):
     dims = (4, 4, 4, 4)
     Us = [synth.gauge_config(dims, 3, 0.3, 1), synth.gauge_config((2, 2, 2, 2), 3, 0.3, 1)]

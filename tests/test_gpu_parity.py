@@ -238,6 +238,32 @@ def test_landau_fix_mixed(cu, orc, nc):
     assert th < 1e-12 and F == pytest.approx(r.F, rel=1e-12)
 
 
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (8, 8, 8, 8)])
+@pytest.mark.parametrize("nc", [2, 3])
+@pytest.mark.parametrize("precision", ["mixed", "mixed_df"])
+def test_landau_fix_automatic_switch(cu, orc, nc, dims, precision):
+    """switch_theta = 0: the FP32 phase runs past theta < 1e-8 until a check
+    interval no longer lowers theta, then the orbit-exact switch and the
+    FP64-class polish to 1e-12. Final F within 1e-10 of the FP64 oracle's,
+    plaquette unchanged to 1e-12, and at least as many FP32 sweeps as with
+    the switch at 1e-8."""
+    prec = cu.MIXED if precision == "mixed" else cu.MIXED_DF
+    U = synth.gauge_config(dims, nc, 0.3, 1)
+    p = cu.Params.defaults(nc, dims, precision=prec, check_every=5, reunit_every=50, max_sweeps=6000,
+                           switch_theta=0.0)
+    d = to_dev(U)
+    r = cu.culgt_landau_fix(d, p)
+    r8 = cu.culgt_landau_fix(to_dev(U), cu.Params(**{**p.__dict__, "switch_theta": 1e-8}))
+    ref = U.copy()
+    rr = orc.landau_fix(ref, dims, nc, 1.7, 1e-12, 6000, 1)
+    assert r.status == cu.OK and r.theta < 1e-12
+    assert r.sweeps_fp32 >= r8.sweeps_fp32 and r.sweeps_fp64 > 0
+    assert r.F == pytest.approx(rr["F"], rel=1e-10)
+    assert r.plaq_after == pytest.approx(r.plaq_before, abs=1e-12)
+    th, F = orc.theta(from_dev(d, U.shape), dims, nc)
+    assert th < 1e-12 and F == pytest.approx(r.F, rel=1e-12)
+
+
 def test_not_converged_status(cu):
     dims = (4, 4, 4, 4)
     U = synth.gauge_config(dims, 3, 0.3, 1)
