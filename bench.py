@@ -52,6 +52,7 @@ BATCHED = {
                                                ((32, 16, 16, 16), 8), ((24, 24, 24, 24), 8)],
     "coulomb_su3_48x48x48x96": None,
     "su3_64x64x64x64": None,
+    "su2_64x64x64x64": None,
     "mag_su3_32x32x32x32": None,
 }
 
@@ -76,6 +77,8 @@ def parse():
     ap.add_argument("--impl", default="culgt", choices=["culgt", "reference"])
     ap.add_argument("--workload", default="su3_32x32x32x32", choices=sorted(WORKLOADS) + sorted(BATCHED))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads (64^4, Gribov batch, Coulomb, MAG, SU(2) 64^4) in the line")
     ap.add_argument("--profile-step", choices=["mixed", "fp64", "fp32", "df", "mixed_df"], default=None,
                     help="run one gauge fixing (or --profile-sweeps sweeps) of the workload and exit; "
                          "the command the ncu captures in profiles/ wrap")
@@ -316,249 +319,372 @@ def run_profile_step(args):
     return 0
 
 
-def run_mag(args):
-    """Maximally Abelian gauge on the 32^4 SU(3) workload: MAG half-sweeps
-    timed back to back (FP32 12-real and FP64 18-real), and whole MAG fixes to
-    theta_MAG < 1e-12, mixed FP32 -> FP64 and plain FP64."""
-    import numpy as np
-    import torch
+class Background:
+    """Generates the large inputs of the other workloads on the host cores, one
+    after the other in a background thread, while the GPU measures; the
+    generator itself runs in spawned worker processes (all cores but two)."""
 
-    import __graft_entry__
-    __graft_entry__.build_library()
-    from paper_1412_3655_gb300 import culgt, synth
+    def __init__(self, jobs):
+        from concurrent.futures import ThreadPoolExecutor
+        self.ex = ThreadPoolExecutor(max_workers=1)
+        self.futs = {name: self.ex.submit(fn) for name, fn in jobs}
+
+    def get(self, name):
+        return self.futs.pop(name).result()
+
+    def close(self):
+        self.ex.shutdown(wait=True)
+
+
+def gen_workers():
+    return max(1, min(os.cpu_count() or 1, 16) - 2)
+
+
+def _gribov_copy(job):
+    import numpy as np
+    from paper_1412_3655_gb300 import synth
+    dims, c = job
+    return synth.gauge_config(dims, 3, 0.3, 4, copy=c, workers=1).view(np.float64).reshape(-1).copy()
+
+
+def gribov_inputs(synth, workers=1):
+    """C4: 64 Haar gauge copies of one SU(3) 16^4 field (eps 0.3, seed 4) and 8
+    copies each of 8^4, 12^4, 16^3 x 32 and 24^4, as flat float64 arrays; the
+    copies generated by `workers` spawned processes."""
+    jobs, dims_list, groups = [], [], []
+    for dims, copies in BATCHED["gribov_su3_16x16x16x16_64copies_uneven"]:
+        for c in range(1, copies + 1):
+            jobs.append((dims, c))
+            dims_list.append(dims)
+            groups.append("x".join(map(str, dims)))
+    if workers > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            inputs = list(ex.map(_gribov_copy, jobs))
+    else:
+        inputs = [_gribov_copy(j) for j in jobs]
+    return dims_list, groups, inputs
+
+
+def _flat(U):
+    import numpy as np
+    return U.view(np.float64).reshape(-1)
+
+
+def timed_fix(culgt, torch, stream, params, d_in, d_out):
+    """(seconds, result) of one whole fix through a handle: load, fix, store;
+    CUDA events on the launching stream."""
+    with culgt.Handle(params, stream) as h:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.culgt_load(d_in)
+        r = h.culgt_handle_fix()
+        h.culgt_store(d_out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3, r
+
+
+def sweep_rate(culgt, torch, stream, params, d_in, n_sweeps, warm=5):
+    """ms per sweep of n_sweeps back-to-back sweeps through a handle (after
+    warm sweeps, which also run the autotuner), and the mapping it used."""
+    with culgt.Handle(params, stream) as h:
+        h.culgt_load(d_in)
+        h.culgt_handle_sweep(warm)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.culgt_handle_sweep(n_sweeps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n_sweeps, h.culgt_handle_tuning()
+
+
+def workload_mag(culgt, torch, stream, d_in, d_out, hbm, src):
+    """Maximally Abelian gauge on the 32^4 SU(3) field: MAG half-sweeps timed
+    back to back (FP32 12-real, FP64 18-real) and whole MAG fixes to
+    theta_MAG < 1e-12, mixed FP32 -> FP64 and plain FP64."""
     dims, nc, eps, seed, omega = WORKLOADS["su3_32x32x32x32"]
-    V = int(np.prod(dims))
-    U = synth.gauge_config(dims, nc, eps, seed)
-    d_in = torch.from_numpy(U.view(np.float64).copy()).cuda()
-    d_out = torch.empty_like(d_in)
-    stream = torch.cuda.current_stream()
-    peaks, src = measured_peaks()
-    hbm = float(peaks["hbm_gbs"])
+    V = dims[0] * dims[1] * dims[2] * dims[3]
     kernels = {}
     for name, prec, bps, n in [("fp32_12", culgt.FP32, 768, 100), ("fp64_18", culgt.FP64, 2304, 20)]:
         p = culgt.Params.defaults(nc, dims, omega=omega, precision=prec, gauge=culgt.MAG)
-        with culgt.Handle(p, stream) as h:
-            h.culgt_load(d_in)
-            h.culgt_handle_sweep(3)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            h.culgt_handle_sweep(n)
-            b.record(stream)
-            torch.cuda.synchronize()
-            ms = a.elapsed_time(b) / (2 * n)
-            gbs = (V // 2) * bps / (ms / 1e3) / 1e9
-            kernels[name] = {"launch_ms": ms, "algorithmic_GB_per_s": gbs, "hbm_frac": gbs / hbm,
-                             "peak_source": f"{src} hbm_gbs",
-                             "traffic": recorded_traffic(f"mag_halfsweep_su3_{name[:3]}_{name[4:]}_b128")}
+        ms, _ = sweep_rate(culgt, torch, stream, p, d_in, n, warm=3)
+        ms /= 2
+        gbs = (V // 2) * bps / (ms / 1e3) / 1e9
+        key = f"mag_halfsweep_su3_{name[:3]}_{name[4:]}_b128"
+        tr = recorded_traffic(key)
+        kernels[name] = {"launch_ms": ms, "algorithmic_GB_per_s": gbs, "hbm_frac": gbs / hbm,
+                         "dram_frac": (tr / (ms / 1e3) / 1e9 / hbm) if tr else None,
+                         "peak_source": f"{src} hbm_gbs", "traffic": tr}
     fixes = {}
     for name, prec in [("mixed", culgt.MIXED), ("fp64", culgt.FP64)]:
         p = culgt.Params.defaults(nc, dims, omega=omega, precision=prec, check_every=10, reunit_every=50,
                                   max_sweeps=20000, gauge=culgt.MAG)
-        with culgt.Handle(p, stream) as h:
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            h.culgt_load(d_in)
-            r = h.culgt_handle_fix()
-            h.culgt_store(d_out)
-            b.record(stream)
-            torch.cuda.synchronize()
-            fixes[name] = {"s": a.elapsed_time(b) / 1e3, "sweeps": [r.sweeps_fp32, r.sweeps_fp64], "theta": r.theta,
-                           "F": r.F, "status": r.status}
-    updates = sum(fixes["mixed"]["sweeps"]) * V
-    line = {
-        "metric": "SU(3) MAG site-updates/s; time to theta_MAG<1e-12 mixed vs plain FP64",
-        "value": updates / fixes["mixed"]["s"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
-        "ms_per_step": 1e3 * fixes["mixed"]["s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32->f64 (mixed)", "data": "synthetic",
-        "config": {"workload": args.workload, "dims": list(dims), "eps": eps, "seed": seed, "omega": omega,
-                   "gauge": "maximally Abelian"},
-        "half_sweeps": kernels, "time_to_theta": fixes,
-    }
-    print(json.dumps(line), flush=True)
-    return 0
+        t, r = timed_fix(culgt, torch, stream, p, d_in, d_out)
+        fixes[name] = {"s": t, "sweeps": [r.sweeps_fp32, r.sweeps_fp64], "theta": r.theta, "F": r.F,
+                       "status": r.status}
+    return {"workload": "SU(3) 32^4, eps 0.3, seed 2, omega 1.7, maximally Abelian gauge",
+            "half_sweeps": kernels, "time_to_theta": fixes,
+            "speedup_mixed_vs_fp64": fixes["fp64"]["s"] / fixes["mixed"]["s"]}
 
 
-def run_large_lattice(args):
-    """SU(3) 64^4 (eps 0.25, seed 3, omega 1.75): 200 timed sweeps in FP64
-    18-real and in FP32 12-real, then whole fixes to theta < 1e-12, mixed
-    FP32 -> FP64 and plain FP64."""
-    import numpy as np
-    import torch
-
-    import __graft_entry__
-    __graft_entry__.build_library()
-    from paper_1412_3655_gb300 import culgt, synth
-    dims, nc, eps, seed, omega = (64, 64, 64, 64), 3, 0.25, 3, 1.75
-    V = int(np.prod(dims))
-    U = synth.gauge_config(dims, nc, eps, seed)
-    d_in = torch.from_numpy(U.view(np.float64).copy()).cuda()
-    del U
-    d_out = torch.empty_like(d_in)
-    stream = torch.cuda.current_stream()
-    peaks, _ = measured_peaks()
+def workload_large(culgt, torch, stream, U, hbm, src, fixes=False):
+    """C3, SU(3) 64^4 (eps 0.25, seed 3, omega 1.75): 200 timed sweeps in FP64
+    18-real and in FP32 12-real; with fixes, whole fixes to theta < 1e-12,
+    mixed FP32 -> FP64 and plain FP64 (about 11 minutes together)."""
+    dims, nc, omega = (64, 64, 64, 64), 3, 1.75
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    d_in = torch.from_numpy(_flat(U)).cuda()
     out = {}
     for name, prec, bps in [("fp64_18", culgt.FP64, 2304), ("fp32_12", culgt.FP32, 768)]:
         p = culgt.Params.defaults(nc, dims, omega=omega, precision=prec)
-        with culgt.Handle(p, stream) as h:
-            h.culgt_load(d_in)
-            h.culgt_handle_sweep(10)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            h.culgt_handle_sweep(200)
-            b.record(stream)
-            torch.cuda.synchronize()
-            ms = a.elapsed_time(b) / 200
-            gbs = V * bps / (ms / 1e3) / 1e9
-            out[name] = {"ms_per_sweep": ms, "site_updates_per_s": V / (ms / 1e3), "GB_per_s": gbs,
-                         "hbm_frac": gbs / float(peaks["hbm_gbs"]), "mapping": h.culgt_handle_tuning()}
-    fixes = {}
-    for name, prec in [("mixed", culgt.MIXED), ("fp64", culgt.FP64)]:
-        p = culgt.Params.defaults(nc, dims, omega=omega, precision=prec, check_every=10, reunit_every=50,
-                                  max_sweeps=40000)
-        with culgt.Handle(p, stream) as h:
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            h.culgt_load(d_in)
-            r = h.culgt_handle_fix()
-            h.culgt_store(d_out)
-            b.record(stream)
-            torch.cuda.synchronize()
-            fixes[name] = {"s": a.elapsed_time(b) / 1e3, "sweeps": [r.sweeps_fp32, r.sweeps_fp64], "theta": r.theta,
-                           "F": r.F, "status": r.status}
-    updates = sum(fixes["mixed"]["sweeps"]) * V
-    line = {
-        "metric": METRIC, "value": updates / fixes["mixed"]["s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
-        "warmup": 0, "ms_per_step": 1e3 * fixes["mixed"]["s"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32->f64 (mixed)", "data": "synthetic",
-        "config": {"workload": args.workload, "dims": list(dims), "eps": eps, "seed": seed, "omega": omega},
-        "timed_sweeps_200": out, "time_to_theta": fixes,
-    }
-    print(json.dumps(line), flush=True)
-    return 0
-
-
-def run_batched_workload(args):
-    """Gribov-copy search or Coulomb gauge through the batched engine: mixed
-    FP32 -> FP64 against plain FP64, time to theta < 1e-12 for every problem."""
-    import numpy as np
-    import torch
-
-    import __graft_entry__
-    __graft_entry__.build_library()
-    from paper_1412_3655_gb300 import culgt, synth
-    dev = torch.device("cuda", 0)
-    nc, eps, omega = 3, 0.3, 1.7
-    if args.workload.startswith("gribov"):
-        dims_list, groups, inputs = [], [], []
-        for dims, copies in BATCHED[args.workload]:
-            for c in range(1, copies + 1):
-                U = synth.gauge_config(dims, nc, eps, 4, copy=c)
-                inputs.append(torch.from_numpy(U.view(np.float64).copy()))
-                dims_list.append(dims)
-                groups.append("x".join(map(str, dims)))
-        sites = sum(int(np.prod(d)) for d in dims_list)
-
-        def run(prec):
-            ds = [t.to(dev) for t in inputs]
-            p = culgt.Params.defaults(nc, dims_list[0], omega=omega, precision=prec, check_every=10,
-                                      reunit_every=50, max_sweeps=20000)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            res = culgt.culgt_fix_batched(ds, dims_list, p)
-            torch.cuda.synchronize()
-            return time.perf_counter() - t0, res, [int(np.prod(d)) for d in dims_list]
-    else:
-        dims = (96, 48, 48, 48)
-        U = synth.gauge_config(dims, nc, eps, 5)
-        host = torch.from_numpy(U.view(np.float64).copy())
-        sites = int(np.prod(dims))
-        groups = [f"t={t}" for t in range(dims[0])]
-
-        def run(prec):
-            d = host.to(dev)
+        ms, m = sweep_rate(culgt, torch, stream, p, d_in, 200, warm=10)
+        gbs = V * bps / (ms / 1e3) / 1e9
+        out[name] = {"ms_per_sweep": ms, "site_updates_per_s": V / (ms / 1e3), "GB_per_s": gbs,
+                     "hbm_frac": gbs / hbm, "peak_source": f"{src} hbm_gbs", "mapping": m}
+    res = {"workload": "SU(3) 64^4, eps 0.25, seed 3, omega 1.75", "timed_sweeps_200": out,
+           "l2": "working set far above L2 (FP32 links 3.2 GB, FP64 links 9.7 GB)"}
+    if fixes:
+        d_out = torch.empty_like(d_in)
+        tt = {}
+        for name, prec in [("mixed", culgt.MIXED), ("fp64", culgt.FP64)]:
             p = culgt.Params.defaults(nc, dims, omega=omega, precision=prec, check_every=10, reunit_every=50,
-                                      max_sweeps=20000)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            res = culgt.culgt_coulomb_fix(d, p)
-            torch.cuda.synchronize()
-            return time.perf_counter() - t0, res, [sites // dims[0]] * dims[0]
+                                      max_sweeps=40000)
+            t, r = timed_fix(culgt, torch, stream, p, d_in, d_out)
+            tt[name] = {"s": t, "sweeps": [r.sweeps_fp32, r.sweeps_fp64], "theta": r.theta, "F": r.F,
+                        "status": r.status}
+        res["time_to_theta"] = tt
+    return res
 
-    run(culgt.MIXED)  # warm-up (autotuning, graph capture)
-    t_mixed, r_mixed, per = run(culgt.MIXED)
-    t_fp64, r_fp64, _ = run(culgt.FP64)
-    anneal = None
-    if args.workload.startswith("gribov"):
-        # simulated annealing before the overrelaxation (the paper's combination
-        # for the Gribov-copy search); copy j draws with seed + j
+
+def workload_su2_large(culgt, torch, stream, U, hbm, src):
+    """SU(2) 64^4 (eps 0.25, seed 3, omega 1.75), a working set well above L2
+    (FP32 quaternion links 1.07 GB): the per-phase half-sweep rates of the
+    mixed schedule and time to theta < 1e-12, mixed against plain FP64."""
+    dims, nc, omega = (64, 64, 64, 64), 2, 1.75
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    d_in = torch.from_numpy(_flat(U)).cuda()
+    d_out = torch.empty_like(d_in)
+    mixed = culgt.Params.defaults(nc, dims, omega=omega, precision=culgt.MIXED, check_every=10, reunit_every=50,
+                                  max_sweeps=40000)
+    plain = culgt.Params(**{**mixed.__dict__, "precision": culgt.FP64})
+    k = {}
+    for name, p, key, n in [("fp32_phase", mixed, (2, 1, 4, "acc"), 200), ("fp64", plain, (2, 0, 4), 50)]:
+        ms, m = sweep_rate(culgt, torch, stream, p, d_in, n)
+        ms /= 2
+        gbs = (V // 2) * BYTES_PER_SITE[key] / (ms / 1e3) / 1e9
+        k[name] = {"launch_ms": ms, "algorithmic_GB_per_s": gbs, "hbm_frac": gbs / hbm,
+                   "peak_source": f"{src} hbm_gbs", "mapping": m,
+                   "working_set_bytes": V * 4 * (16 if name == "fp32_phase" else 32) + (V * 16 if name == "fp32_phase"
+                                                                                       else 0)}
+    tt = {}
+    for name, p in [("mixed", mixed), ("fp64", plain)]:
+        t, r = timed_fix(culgt, torch, stream, p, d_in, d_out)
+        tt[name] = {"s": t, "sweeps": [r.sweeps_fp32, r.sweeps_fp64], "F": r.F, "status": r.status}
+    return {"workload": "SU(2) 64^4, eps 0.25, seed 3, omega 1.75", "half_sweeps": k, "time_to_theta": tt}
+
+
+def workload_gribov(culgt, torch, np, stream, dims_list, groups, inputs, anneal=True):
+    """C4 through the batched engine: every copy in shared launches, mixed
+    FP32 -> FP64 against plain FP64, time to theta < 1e-12 for every problem,
+    max F per lattice size; with anneal, simulated annealing before the
+    overrelaxation (copy j keyed by seed + j)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    nc, omega = 3, 1.7
+    per = [int(np.prod(d)) for d in dims_list]
+
+    def run(prec, switch=1e-8):
+        ds = [torch.from_numpy(t).to(dev) for t in inputs]
+        p = culgt.Params.defaults(nc, dims_list[0], omega=omega, precision=prec, check_every=10,
+                                  reunit_every=50, max_sweeps=20000, switch_theta=switch)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = culgt.culgt_fix_batched(ds, dims_list, p, stream)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, res
+
+    run(culgt.MIXED)  # warm-up (graph capture)
+    t_mixed, r_mixed = run(culgt.MIXED)
+    t_fp64, r_fp64 = run(culgt.FP64)
+    t_auto, r_auto = run(culgt.MIXED, culgt.SWITCH_AUTO)
+    maxF, maxF64 = {}, {}
+    for g, r, q in zip(groups, r_mixed, r_fp64):
+        maxF[g] = max(maxF.get(g, -1.0), r.F)
+        maxF64[g] = max(maxF64.get(g, -1.0), q.F)
+    updates = sum((r.sweeps_fp32 + r.sweeps_fp64) * n for r, n in zip(r_mixed, per))
+    out = {
+        "workload": "64 Haar copies of one SU(3) 16^4 field (eps 0.3, seed 4) + 8 copies each of 8^4, 12^4, "
+                    "16^3x32, 24^4; 96 problems in shared launches",
+        "problems": len(r_mixed), "sites": sum(per),
+        "time_to_theta": {"mixed_s": t_mixed, "fp64_s": t_fp64, "mixed_auto_switch_s": t_auto,
+                          "speedup_mixed_vs_fp64": t_fp64 / t_mixed},
+        "site_updates_per_s_mixed": updates / t_mixed,
+        "all_converged": {"mixed": all(r.status == culgt.OK for r in r_mixed),
+                          "fp64": all(r.status == culgt.OK for r in r_fp64),
+                          "mixed_auto": all(r.status == culgt.OK for r in r_auto)},
+        "max_F": maxF, "max_F_fp64": maxF64,
+        "mixed_vs_fp64_max_dF": max(abs(a.F - b.F) for a, b in zip(r_mixed, r_fp64)),
+        "plaquette_drift_max": max(abs(r.plaq_after - r.plaq_before) for r in r_mixed),
+    }
+    if anneal:
         a = culgt.culgt_default_anneal_params()
         a.seed = 11
-        ds = [t.to(dev) for t in inputs]
+        ds = [torch.from_numpy(t).to(dev) for t in inputs]
         p = culgt.Params.defaults(nc, dims_list[0], omega=omega, precision=culgt.MIXED, check_every=10,
                                   reunit_every=50, max_sweeps=20000)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r_ann = culgt.culgt_fix_batched_anneal(ds, dims_list, p, a)
+        r_ann = culgt.culgt_fix_batched_anneal(ds, dims_list, p, a, stream)
         torch.cuda.synchronize()
         t_ann = time.perf_counter() - t0
-        best_plain, best_ann = {}, {}
-        for g, r0, r1 in zip(groups, r_mixed, r_ann):
-            best_plain[g] = max(best_plain.get(g, -1.0), r0.F)
-            best_ann[g] = max(best_ann.get(g, -1.0), r1.F)
+        best = {}
+        for g, r1 in zip(groups, r_ann):
+            best[g] = max(best.get(g, -1.0), r1.F)
         sa_sweeps = a.steps * (1 + a.micro_sweeps)
-        anneal = {
+        out["anneal"] = {
             "schedule": {"t_start": a.t_start, "t_end": a.t_end, "steps": a.steps, "micro_sweeps": a.micro_sweeps,
                          "seed": a.seed},
             "s": t_ann, "all_converged": all(r.status == culgt.OK for r in r_ann),
             "site_updates_per_s": sum((sa_sweeps + r.sweeps_fp32 + r.sweeps_fp64) * n
                                       for r, n in zip(r_ann, per)) / t_ann,
-            "mean_F": float(np.mean([r.F for r in r_ann])), "mean_F_without": float(np.mean([r.F for r in r_mixed])),
-            "max_F": best_ann, "max_F_without": best_plain,
-            "copies_above_without": float(np.mean([r1.F > r0.F + 1e-12 for r0, r1 in zip(r_mixed, r_ann)])),
-        }
-        # a rougher field (eps 0.6), where overrelaxation alone ends on
-        # different local maxima from different copies
-        rough_dims = (8, 8, 8, 8)
-        rough = [torch.from_numpy(synth.gauge_config(rough_dims, nc, 0.6, 4, copy=c).view(np.float64).copy())
-                 for c in range(32)]
-        pr = culgt.Params.defaults(nc, rough_dims, omega=omega, precision=culgt.MIXED, check_every=10,
-                                   reunit_every=50, max_sweeps=50000)
-        r0 = culgt.culgt_fix_batched([t.to(dev) for t in rough], [rough_dims] * 32, pr)
-        t0 = time.perf_counter()
-        r1 = culgt.culgt_fix_batched_anneal([t.to(dev) for t in rough], [rough_dims] * 32, pr, a)
+            "max_F": best}
+    return out
+
+
+def workload_batched_cost(culgt, torch, np, stream, dims_list, groups, inputs, n1=60, n2=240):
+    """What the batched engine's design (one launch per colour over the tiles
+    of every active problem, each check interval replayed as a CUDA graph)
+    costs on the C4 mix. Per lattice-size group, the engine's time per FP32
+    12-real sweep of the whole group, taken as the difference of runs of n2
+    and n1 sweeps (so the call's fixed cost, allocation and layout
+    conversion, drops out), against the same sweeps of each lattice alone
+    through a single-lattice handle (sweeps back to back, so a lattice whose
+    links fit in L2 runs from L2 there). The fixed cost of a colour launch is
+    the engine's time per sweep (two launches) of 64 lattices of 2^4 sites."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {}
+    order = []
+    for g in groups:
+        if g not in order:
+            order.append(g)
+
+    def per_sweep_s(ds, dl):
+        ts = []
+        for n in (n1, n2):
+            p = culgt.Params.defaults(3, dl[0], precision=culgt.FP32, theta_target=0.0, max_sweeps=n,
+                                      check_every=30, reunit_every=0)
+            culgt.culgt_fix_batched(ds, dl, p, stream)  # warm-up (graph capture)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            culgt.culgt_fix_batched(ds, dl, p, stream)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return (ts[1] - ts[0]) / (n2 - n1)
+
+    for g in order + ["all"]:
+        idx = [i for i, gg in enumerate(groups) if gg == g or g == "all"]
+        dl = [dims_list[i] for i in idx]
+        ds = [torch.from_numpy(inputs[i]).to(dev) for i in idx]
+        sites = sum(int(np.prod(d)) for d in dl)
+        tb = per_sweep_s(ds, dl)
+        rec = {"problems": len(idx), "sites": sites, "batched_ms_per_sweep": 1e3 * tb,
+               "batched_site_updates_per_s": sites / tb,
+               "batched_GB_per_s": sites * BYTES_PER_SITE[(3, 1, 12)] / tb / 1e9}
+        if g != "all":
+            p = culgt.Params.defaults(3, dl[0], precision=culgt.FP32)
+            ts = 0.0
+            for d in ds:
+                ms, m = sweep_rate(culgt, torch, stream, p, d, n2, warm=3)
+                ts += ms / 1e3
+            one = int(np.prod(dl[0])) * 4 * 48
+            rec.update({"single_ms_per_sweep": 1e3 * ts, "single_site_updates_per_s": sites / ts,
+                        "batched_over_single": ts / tb, "single_mapping": m,
+                        "single_lattice_links_bytes": one, "single_lattice_in_l2": one < L2_BYTES})
+        out[g] = rec
+    tiny = [(2, 2, 2, 2)] * 64
+    from paper_1412_3655_gb300 import synth
+    base = _flat(synth.gauge_config((2, 2, 2, 2), 3, 0.3, 4)).copy()
+    out["fixed_cost_per_colour_launch_us"] = 1e6 * per_sweep_s([torch.from_numpy(base).to(dev) for _ in tiny],
+                                                               tiny) / 2
+    out["note"] = ("FP32 12-real sweeps, theta every 30 sweeps (one graph replay each), per-sweep time from "
+                   "two run lengths; "
+                   "single: each lattice alone through a handle, the group's lattices one after another")
+    return out
+
+
+def workload_coulomb(culgt, torch, stream, U):
+    """C5: SU(3) Coulomb gauge on 48^3 x 96 (eps 0.3, seed 5, omega 1.7), one
+    problem per time slice in shared launches, each retired at its own
+    theta < 1e-12: mixed FP32 -> FP64 against plain FP64."""
+    dims, nc, omega = (96, 48, 48, 48), 3, 1.7
+    host = torch.from_numpy(_flat(U))
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def run(prec, switch=1e-8):
+        d = host.to(dev)
+        p = culgt.Params.defaults(nc, dims, omega=omega, precision=prec, check_every=10, reunit_every=50,
+                                  max_sweeps=20000, switch_theta=switch)
         torch.cuda.synchronize()
-        anneal["rough_field"] = {
-            "workload": "32 gauge copies of one 8^4 SU(3) field, eps 0.6", "s": time.perf_counter() - t0,
-            "all_converged": all(r.status == culgt.OK for r in r0 + r1),
-            "mean_F": float(np.mean([r.F for r in r1])), "mean_F_without": float(np.mean([r.F for r in r0])),
-            "max_F": max(r.F for r in r1), "max_F_without": max(r.F for r in r0),
-            "distinct_maxima_without": len({round(r.F, 9) for r in r0}),
-            "distinct_maxima": len({round(r.F, 9) for r in r1}),
-        }
-    updates = sum((r.sweeps_fp32 + r.sweeps_fp64) * n for r, n in zip(r_mixed, per))
-    maxF = {}
-    for g, r in zip(groups, r_mixed):
-        maxF[g] = max(maxF.get(g, -1.0), r.F)
-    line = {
-        "metric": METRIC, "value": updates / t_mixed, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
-        "ms_per_step": 1e3 * t_mixed, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32->f64 (mixed)", "data": "synthetic",
-        "config": {"workload": args.workload, "problems": len(r_mixed), "sites": sites, "eps": eps,
-                   "omega": omega, "theta_target": 1e-12, "switch_theta": 1e-8},
-        "time_to_theta": {"mixed_s": t_mixed, "fp64_s": t_fp64},
-        "all_converged": {"mixed": all(r.status == culgt.OK for r in r_mixed),
-                          "fp64": all(r.status == culgt.OK for r in r_fp64)},
-        "sweeps_mixed": {"fp32_min": min(r.sweeps_fp32 for r in r_mixed),
-                         "fp32_max": max(r.sweeps_fp32 for r in r_mixed),
-                         "fp64_min": min(r.sweeps_fp64 for r in r_mixed),
-                         "fp64_max": max(r.sweeps_fp64 for r in r_mixed)},
-        "max_F": maxF if len(maxF) <= 8 else None,
-        "F_range": [min(r.F for r in r_mixed), max(r.F for r in r_mixed)],
-        "mixed_vs_fp64_max_dF": max(abs(a.F - b.F) for a, b in zip(r_mixed, r_fp64)),
-        "plaquette_drift_max": max(abs(r.plaq_after - r.plaq_before) for r in r_mixed),
-    }
-    if anneal:
-        line["anneal"] = anneal
+        t0 = time.perf_counter()
+        res = culgt.culgt_coulomb_fix(d, p, stream)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, res
+
+    t_mixed, r_mixed = run(culgt.MIXED)
+    t_fp64, r_fp64 = run(culgt.FP64)
+    t_auto, r_auto = run(culgt.MIXED, culgt.SWITCH_AUTO)
+    V3 = 48 ** 3
+    updates = sum((r.sweeps_fp32 + r.sweeps_fp64) * V3 for r in r_mixed)
+    return {"workload": "SU(3) Coulomb gauge, 48^3 x 96, eps 0.3, seed 5, omega 1.7: 96 slices in shared launches",
+            "time_to_theta": {"mixed_s": t_mixed, "fp64_s": t_fp64, "mixed_auto_switch_s": t_auto,
+                              "speedup_mixed_vs_fp64": t_fp64 / t_mixed},
+            "site_updates_per_s_mixed": updates / t_mixed,
+            "all_converged": {"mixed": all(r.status == culgt.OK for r in r_mixed),
+                              "fp64": all(r.status == culgt.OK for r in r_fp64),
+                              "mixed_auto": all(r.status == culgt.OK for r in r_auto)},
+            "sweeps_mixed": {"fp32_max": max(r.sweeps_fp32 for r in r_mixed),
+                             "fp64_max": max(r.sweeps_fp64 for r in r_mixed)},
+            "mixed_vs_fp64_max_dF": max(abs(a.F - b.F) for a, b in zip(r_mixed, r_fp64)),
+            "plaquette_drift_max": abs(r_mixed[0].plaq_after - r_mixed[0].plaq_before)}
+
+
+def run_workload(args):
+    """One of the other workloads alone, as its own JSON line."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1412_3655_gb300 import culgt, synth
+    stream = torch.cuda.current_stream()
+    peaks, src = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    w = args.workload
+    if w == "mag_su3_32x32x32x32":
+        dims, nc, eps, seed, _ = WORKLOADS["su3_32x32x32x32"]
+        d_in = torch.from_numpy(_flat(synth.gauge_config(dims, nc, eps, seed)).copy()).cuda()
+        res = workload_mag(culgt, torch, stream, d_in, torch.empty_like(d_in), hbm, src)
+        value = sum(res["time_to_theta"]["mixed"]["sweeps"]) * 32 ** 4 / res["time_to_theta"]["mixed"]["s"]
+    elif w == "su3_64x64x64x64":
+        res = workload_large(culgt, torch, stream, synth.gauge_config((64,) * 4, 3, 0.25, 3), hbm, src, fixes=True)
+        tt = res["time_to_theta"]["mixed"]
+        value = sum(tt["sweeps"]) * 64 ** 4 / tt["s"]
+    elif w == "su2_64x64x64x64":
+        res = workload_su2_large(culgt, torch, stream, synth.gauge_config((64,) * 4, 2, 0.25, 3), hbm, src)
+        tt = res["time_to_theta"]["mixed"]
+        value = sum(tt["sweeps"]) * 64 ** 4 / tt["s"]
+    elif w.startswith("gribov"):
+        dl, groups, inputs = gribov_inputs(synth, gen_workers())
+        res = workload_gribov(culgt, torch, np, stream, dl, groups, inputs)
+        res["batched_engine_cost"] = workload_batched_cost(culgt, torch, np, stream, dl, groups, inputs)
+        value = res["site_updates_per_s_mixed"]
+    else:
+        res = workload_coulomb(culgt, torch, stream, synth.gauge_config((96, 48, 48, 48), 3, 0.3, 5))
+        value = res["site_updates_per_s_mixed"]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32->f64 (mixed)",
+            "data": "synthetic", "config": {"workload": w}, **res}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -622,6 +748,18 @@ def run_culgt(args):
     barrier()
     launches = culgt.culgt_kernel_launches() - launches0
     clocks = sampler.stop()
+    extras = ws == 1 and not args.no_extras
+    bg = None
+    if extras:
+        # inputs of the other workloads, generated on the host while the GPU
+        # measures what follows (the timed region above is over)
+        w = gen_workers()
+        bg = Background([
+            ("gribov", lambda: gribov_inputs(synth, w)),
+            ("su3_64", lambda: synth.gauge_config((64, 64, 64, 64), 3, 0.25, 3, workers=w)),
+            ("su2_64", lambda: synth.gauge_config((64, 64, 64, 64), 2, 0.25, 3, workers=w)),
+            ("coulomb", lambda: synth.gauge_config((96, 48, 48, 48), 3, 0.3, 5, workers=w)),
+        ])
     ms = e0.elapsed_time(e1)
     updates = sum((r.sweeps_fp32 + r.sweeps_fp64) * V for r in results)
     ms, updates_all = aggregate(ms, updates, ws, dev)
@@ -657,9 +795,14 @@ def run_culgt(args):
         achieved = bytes_launch / (t_ms / 1e3) / 1e9
         name = (f"halfsweep_su{key[0]}_{'f32' if key[1] else 'f64'}_{key[2]}" + ("_acc" if len(key) > 3 else "")
                 + f"_tps{m[0]}_b{m[1]}_mb{m[2]}")
+        tr = recorded_traffic(name)
         return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": recorded_traffic(name), "kernel": name, "launch_ms": t_ms,
+                "traffic": tr, "dram_frac": dram_frac(tr, t_ms), "kernel": name, "launch_ms": t_ms,
                 "algorithmic_bytes_per_launch": bytes_launch, "peak_source": f"{peak_src} hbm_gbs"}
+
+    def dram_frac(traffic, t_ms):
+        # measured DRAM bytes of the kernel (ncu, per launch) over its launch time
+        return traffic / (t_ms / 1e3) / 1e9 / hbm if traffic else None
 
     def roofline_fp64(key, t_ms, m):
         # FP64-ALU bound on GB300: algorithmic FP64 flops per site update
@@ -668,7 +811,8 @@ def run_culgt(args):
         achieved = flops_launch / (t_ms / 1e3) / 1e12
         name = f"halfsweep_su{key[0]}_{'f32' if key[1] else 'f64'}_{key[2]}_tps{m[0]}_b{m[1]}_mb{m[2]}"
         return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(name), "kernel": name,
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(name),
+                "dram_frac": dram_frac(recorded_traffic(name), t_ms), "kernel": name,
                 "launch_ms": t_ms, "algorithmic_flops_per_launch": flops_launch,
                 "algorithmic_bytes_per_launch": (V // 2) * BYTES_PER_SITE[key],
                 "hbm_frac": (V // 2) * BYTES_PER_SITE[key] / (t_ms / 1e3) / 1e9 / hbm,
@@ -721,14 +865,17 @@ def run_culgt(args):
     rldf = roofline_hbm((nc, 0, 18 if nc == 3 else 4), tdf, mapping["double_float"])
     rldf["kernel"] = rldf["kernel"].replace("f64", "df")
     rldf["traffic"] = recorded_traffic(rldf["kernel"])
+    rldf["dram_frac"] = dram_frac(rldf["traffic"], tdf)
     mk = mapping["heatbath_fp32_phase"]
     rlhb32 = roofline_hbm((nc, 1, 12 if nc == 3 else 4, "acc"), thb32, mk)
     rlhb32["kernel"] = rlhb32["kernel"].replace("halfsweep", "heatbath").replace(f"_tps{mk[0]}_", f"_keep{mk[0]}_")
     rlhb32["traffic"] = recorded_traffic(rlhb32["kernel"])
+    rlhb32["dram_frac"] = dram_frac(rlhb32["traffic"], thb32)
     mk = mapping["heatbath_fp64"]
     rlhb64 = roofline_fp64((nc, 0, 18 if nc == 3 else 4), thb64, mk)
     rlhb64["kernel"] = rlhb64["kernel"].replace("halfsweep", "heatbath").replace(f"_tps{mk[0]}_", f"_keep{mk[0]}_")
     rlhb64["traffic"] = recorded_traffic(rlhb64["kernel"])
+    rlhb64["dram_frac"] = dram_frac(rlhb64["traffic"], thb64)
     rlhb64["note"] = "flops counted as for the overrelaxation update; the draw adds its own"
     # the FP32 -> FP64 switch later: the orbit-exact switch keeps the FP32
     # rounding off the result, so the FP32 phase may run to a lower theta
@@ -736,6 +883,18 @@ def run_culgt(args):
     for sw in (1e-10, 1e-11):
         t_sw, r_sw = fix_time(culgt.Params(**{**mixed.__dict__, "switch_theta": sw}))
         late[f"{sw:g}"] = {"s": t_sw, "sweeps": [r_sw.sweeps_fp32, r_sw.sweeps_fp64], "F": r_sw.F, "theta": r_sw.theta}
+    # the automatic switch (switch_theta = 0): the FP32 phase runs until a
+    # check interval no longer lowers theta, FP64 or double-float polish after
+    auto = {}
+    for name, prec in [("mixed", culgt.MIXED), ("mixed_df", culgt.MIXED_DF)]:
+        t_a, r_a = fix_time(culgt.Params(**{**mixed.__dict__, "precision": prec,
+                                            "switch_theta": culgt.SWITCH_AUTO}))
+        auto[name] = {"s": t_a, "sweeps": [r_a.sweeps_fp32, r_a.sweeps_fp64], "F": r_a.F, "theta": r_a.theta,
+                      "status": r_a.status, "site_updates_per_s": (r_a.sweeps_fp32 + r_a.sweeps_fp64) * V / t_a}
+    # FP64 with 12-real storage (third row rebuilt): 2/3 of the bytes, more FP64 arithmetic
+    plain12 = culgt.Params(**{**plain.__dict__, "storage_reals": 12})
+    t64_12 = kernel_ms(plain12, 20, prefix="s12_")
+    rl64_12 = roofline_fp64((nc, 0, 12), t64_12, mapping["s12_fp64"])
 
     # SU(2) on the same generator (eps 0.3, Haar g, seed 2) and lattice: the
     # per-phase half-sweep rates and the time to theta < 1e-12, mixed vs FP64
@@ -798,8 +957,9 @@ def run_culgt(args):
                                   "double-float sweeps (float pairs, ~48-bit) with theta/F in FP64; "
                                   "mixed_switch_later: the same schedule with the FP32 phase run to a lower theta"},
         "roofline": dominant,
-        "roofline_kernels": {"fp32_phase": rl32, "fp64": rl64, "double_float": rldf,
+        "roofline_kernels": {"fp32_phase": rl32, "fp64": rl64, "fp64_12": rl64_12, "double_float": rldf,
                              "heatbath_fp32_phase": rlhb32, "heatbath_fp64": rlhb64},
+        "auto_switch": auto,
         "su2": su2,
         "gpu_launches": launches,
         "sweep_mapping": {k: ({"keep_links": v[0], "block": v[1], "min_blocks_per_sm": v[2]} if
@@ -810,9 +970,26 @@ def run_culgt(args):
                 "d2h_bytes_per_step": canon_bytes, "steps": n_e2e},
         "clocks": clocks,
     }
+    h.close()
+    if extras:
+        line["mag_su3_32x32x32x32"] = workload_mag(culgt, torch, stream, d_in, d_out, hbm, peak_src)
+        dl, groups, inputs = bg.get("gribov")
+        gr = workload_gribov(culgt, torch, np, stream, dl, groups, inputs)
+        gr["batched_engine_cost"] = workload_batched_cost(culgt, torch, np, stream, dl, groups, inputs)
+        line["gribov_batch"] = gr
+        del inputs
+        line["su3_64x64x64x64"] = workload_large(culgt, torch, stream, bg.get("su3_64"), hbm, peak_src)
+        torch.cuda.empty_cache()
+        line["su2_64x64x64x64"] = workload_su2_large(culgt, torch, stream, bg.get("su2_64"), hbm, peak_src)
+        torch.cuda.empty_cache()
+        line["coulomb_48x48x48x96"] = workload_coulomb(culgt, torch, stream, bg.get("coulomb"))
+        bg.close()
+        line["extras_note"] = ("other workloads, each measured once after the timed region: MAG on the same "
+                               "field; the batched Gribov search (C4), 64^4 SU(3) sweep rates (C3; its whole "
+                               "fixes, about 11 minutes, run with --workload su3_64x64x64x64), SU(2) 64^4 and "
+                               "Coulomb 48^3x96 (C5)")
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(U, dims, nc, omega)
-    h.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -826,12 +1003,8 @@ def main():
         return run_reference(args)
     if args.profile_step:
         return run_profile_step(args)
-    if args.workload == "su3_64x64x64x64":
-        return run_large_lattice(args)
-    if args.workload == "mag_su3_32x32x32x32":
-        return run_mag(args)
     if args.workload in BATCHED:
-        return run_batched_workload(args)
+        return run_workload(args)
     return run_culgt(args)
 
 
