@@ -91,6 +91,7 @@ def parse():
     ap.add_argument("--tps", type=int, default=0, help="with --profile-step: threads per site (0 = autotune)")
     ap.add_argument("--block", type=int, default=0, help="with --profile-step: threads per block (0 = autotune)")
     ap.add_argument("--minb", type=int, default=0, help="with --profile-step: min blocks per SM (0 = autotune)")
+    ap.add_argument("--storage", type=int, default=0, help="with --profile-step: reals per link (0 = default)")
     return ap.parse_args()
 
 
@@ -297,7 +298,7 @@ def run_profile_step(args):
             "mixed_df": culgt.MIXED_DF}[args.profile_step]
     p = culgt.Params.defaults(nc, dims, omega=omega, precision=prec, check_every=10, reunit_every=50,
                               max_sweeps=20000, threads_per_site=args.tps, block_size=args.block,
-                              min_blocks_per_sm=args.minb,
+                              min_blocks_per_sm=args.minb, storage_reals=args.storage,
                               gauge=culgt.MAG if args.profile_gauge == "mag" else culgt.LANDAU)
     with culgt.Handle(p) as h:
         h.culgt_load(d_in)

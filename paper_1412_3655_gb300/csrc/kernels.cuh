@@ -144,6 +144,25 @@ __device__ __forceinline__ void su3_update(typename P::Chunk *base, const Geom &
             apply_right_adj<P>(t, u, G);
             P::store(bp, g.stride, t);
         }
+    } else if constexpr (!KEEP && P::NREAL == 18) {
+        // 18-real links re-read (FP64): one copy of the update for all
+        // directions, so the compiler does not hoist the next directions'
+        // loads into registers the update needs (it spilled to local memory
+        // unrolled); the same arithmetic, so the links are the same
+#pragma unroll 1
+        for (int k = 0; k < NMU; k++) {
+            const int mu = mu0 + k;
+            if (mu < mu_first || !valid) continue;
+            C *fp = base + plane_offset(g, p, mu, P::NCHUNK) + cb;
+            C *bp = base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1);
+            M3<T> u, t;
+            P::load(fp, g.stride, u);
+            apply_left<P>(t, G, u);
+            P::store(fp, g.stride, t);
+            P::load(bp, g.stride, u);
+            apply_right_adj<P>(t, u, G);
+            P::store(bp, g.stride, t);
+        }
     } else {
 #pragma unroll
         for (int k = 0; k < NMU; k++) {
