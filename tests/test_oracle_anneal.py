@@ -1,7 +1,7 @@
 """Pins of the oracle's simulated annealing (heat bath over the SU(2)
 subgroups, readings R7-R11 of culgt_oracle.c).
 
-The paper names the combination of simulated annealing and overrelaxation
+The paper names simulated annealing combined with overrelaxation
 (abstract, Sec. 1) but prints no formula for it, so every pin comes from the
 mathematics: published test vectors of the random-number generator, the
 exact heat-bath distribution of one SU(2) element (its mean is a ratio of
