@@ -48,3 +48,30 @@ def test_cpu_baseline_record(orc):
     assert r["value"] > 0 and r["cores"] >= 1 and "sweeps" in r["sample"]
     assert r["one_core"]["value"] > 0
     assert orc.get_threads() == r["cores"]
+
+
+def test_background_inputs_come_back_by_name():
+    """The other workloads' inputs are generated one after another in a
+    background thread and handed out by name, whatever order they are asked
+    for in."""
+    order = []
+
+    def job(name):
+        def run():
+            order.append(name)
+            return name * 2
+        return run
+
+    bg = bench.Background([("a", job("a")), ("b", job("b")), ("c", job("c"))])
+    assert bg.get("c") == "cc" and bg.get("a") == "aa" and bg.get("b") == "bb"
+    bg.close()
+    assert order == ["a", "b", "c"]
+    assert 1 <= bench.gen_workers() <= 14
+
+
+def test_gribov_copies_match_the_generator():
+    """A copy of the batched Gribov workload is the generator's own copy."""
+    dims = (4, 4, 4, 4)
+    a = bench._gribov_copy((dims, 3))
+    b = synth.gauge_config(dims, 3, 0.3, 4, copy=3)
+    assert np.array_equal(a, b.view(np.float64).reshape(-1))
