@@ -68,8 +68,10 @@ __device__ __forceinline__ void b_accumulate(const BProb &pr, int cb, int p, int
                 Ga.im[i][j] = (A)G.im[i][j];
             }
         PG::load(gp, pr.g.stride, a);
-        m3_mul_rows<0, 1>(b, Ga, a);
-        if constexpr (PG::NREAL == 18) m3_rebuild_row2(b);
+        // double-float: the exactly summed products (nothing reunitarises
+        // the accumulator between sweeps)
+        m3_mul_rows<0, 1, dfacc>(b, Ga, a);
+        if constexpr (PG::NREAL == 18) m3_rebuild_row2<dfacc>(b);
         PG::store(gp, pr.g.stride, b);
     }
 }

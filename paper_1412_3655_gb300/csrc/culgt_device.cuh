@@ -160,29 +160,34 @@ template <typename T> __device__ __forceinline__ void m3_renorm(M3<T> &a)
 // a third more FP64 instructions, and FP64 is GB300's scarce pipe).
 
 // rows R0..R1 of c = a b  (R1 = 2: the full product)
-template <int R0, int R1, typename T>
+template <int R0, int R1, class Acc = dfsum1, typename T>
 __device__ __forceinline__ void m3_mul_rows(M3<T> &c, const M3<T> &a, const M3<T> &b)
 {
     if constexpr (std::is_same<T, dfl>::value) {
         // double-float: each real output one compensated sum of six products
+        // (Acc: dfsum1, or dfacc for the exactly summed variant)
 #pragma unroll
         for (int i = R0; i <= R1; i++)
 #pragma unroll
             for (int j = 0; j < 3; j++) {
-                dfacc sr = dfacc_mul(a.re[i][0], b.re[0][j]);
-                dfacc_fma(sr, -a.im[i][0], b.im[0][j]);
-                dfacc_fma(sr, a.re[i][1], b.re[1][j]);
-                dfacc_fma(sr, -a.im[i][1], b.im[1][j]);
-                dfacc_fma(sr, a.re[i][2], b.re[2][j]);
-                dfacc_fma(sr, -a.im[i][2], b.im[2][j]);
-                dfacc si = dfacc_mul(a.re[i][0], b.im[0][j]);
-                dfacc_fma(si, a.im[i][0], b.re[0][j]);
-                dfacc_fma(si, a.re[i][1], b.im[1][j]);
-                dfacc_fma(si, a.im[i][1], b.re[1][j]);
-                dfacc_fma(si, a.re[i][2], b.im[2][j]);
-                dfacc_fma(si, a.im[i][2], b.re[2][j]);
-                c.re[i][j] = dfacc_get(sr);
-                c.im[i][j] = dfacc_get(si);
+                Acc sr;
+                acc_init(sr);
+                acc_fma(sr, a.re[i][0], b.re[0][j]);
+                acc_fma(sr, -a.im[i][0], b.im[0][j]);
+                acc_fma(sr, a.re[i][1], b.re[1][j]);
+                acc_fma(sr, -a.im[i][1], b.im[1][j]);
+                acc_fma(sr, a.re[i][2], b.re[2][j]);
+                acc_fma(sr, -a.im[i][2], b.im[2][j]);
+                Acc si;
+                acc_init(si);
+                acc_fma(si, a.re[i][0], b.im[0][j]);
+                acc_fma(si, a.im[i][0], b.re[0][j]);
+                acc_fma(si, a.re[i][1], b.im[1][j]);
+                acc_fma(si, a.im[i][1], b.re[1][j]);
+                acc_fma(si, a.re[i][2], b.im[2][j]);
+                acc_fma(si, a.im[i][2], b.re[2][j]);
+                c.re[i][j] = acc_get(sr);
+                c.im[i][j] = acc_get(si);
             }
         return;
     }
@@ -208,7 +213,7 @@ __device__ __forceinline__ void m3_mul_rows(M3<T> &c, const M3<T> &a, const M3<T
 }
 
 // rows R0..R1 of c = a b^+, (a b^+)_ij = sum_k a_ik conj(b_jk)
-template <int R0, int R1, typename T>
+template <int R0, int R1, class Acc = dfsum1, typename T>
 __device__ __forceinline__ void m3_mul_adj_rows(M3<T> &c, const M3<T> &a, const M3<T> &b)
 {
     if constexpr (std::is_same<T, dfl>::value) {
@@ -216,20 +221,24 @@ __device__ __forceinline__ void m3_mul_adj_rows(M3<T> &c, const M3<T> &a, const 
         for (int i = R0; i <= R1; i++)
 #pragma unroll
             for (int j = 0; j < 3; j++) {
-                dfacc sr = dfacc_mul(a.re[i][0], b.re[j][0]);
-                dfacc_fma(sr, a.im[i][0], b.im[j][0]);
-                dfacc_fma(sr, a.re[i][1], b.re[j][1]);
-                dfacc_fma(sr, a.im[i][1], b.im[j][1]);
-                dfacc_fma(sr, a.re[i][2], b.re[j][2]);
-                dfacc_fma(sr, a.im[i][2], b.im[j][2]);
-                dfacc si = dfacc_mul(a.im[i][0], b.re[j][0]);
-                dfacc_fma(si, -a.re[i][0], b.im[j][0]);
-                dfacc_fma(si, a.im[i][1], b.re[j][1]);
-                dfacc_fma(si, -a.re[i][1], b.im[j][1]);
-                dfacc_fma(si, a.im[i][2], b.re[j][2]);
-                dfacc_fma(si, -a.re[i][2], b.im[j][2]);
-                c.re[i][j] = dfacc_get(sr);
-                c.im[i][j] = dfacc_get(si);
+                Acc sr;
+                acc_init(sr);
+                acc_fma(sr, a.re[i][0], b.re[j][0]);
+                acc_fma(sr, a.im[i][0], b.im[j][0]);
+                acc_fma(sr, a.re[i][1], b.re[j][1]);
+                acc_fma(sr, a.im[i][1], b.im[j][1]);
+                acc_fma(sr, a.re[i][2], b.re[j][2]);
+                acc_fma(sr, a.im[i][2], b.im[j][2]);
+                Acc si;
+                acc_init(si);
+                acc_fma(si, a.im[i][0], b.re[j][0]);
+                acc_fma(si, -a.re[i][0], b.im[j][0]);
+                acc_fma(si, a.im[i][1], b.re[j][1]);
+                acc_fma(si, -a.re[i][1], b.im[j][1]);
+                acc_fma(si, a.im[i][2], b.re[j][2]);
+                acc_fma(si, -a.re[i][2], b.im[j][2]);
+                c.re[i][j] = acc_get(sr);
+                c.im[i][j] = acc_get(si);
             }
         return;
     }
@@ -268,22 +277,26 @@ template <typename T> __device__ __forceinline__ void m3_mul_adj(M3<T> &c, const
 
 // row 2 = conj(row 0 x row 1): the third row of an SU(3) matrix from its
 // first two (the 12-parameter reconstruction, Sec. 3.1)
-template <typename T> __device__ __forceinline__ void m3_rebuild_row2(M3<T> &u)
+template <class Acc = dfsum1, typename T> __device__ __forceinline__ void m3_rebuild_row2(M3<T> &u)
 {
     if constexpr (std::is_same<T, dfl>::value) {
 #pragma unroll
         for (int b = 0; b < 3; b++) {
             const int c = (b + 1) % 3, d = (b + 2) % 3;
-            dfacc xr = dfacc_mul(u.re[0][c], u.re[1][d]);
-            dfacc_fma(xr, -u.im[0][c], u.im[1][d]);
-            dfacc_fma(xr, -u.re[0][d], u.re[1][c]);
-            dfacc_fma(xr, u.im[0][d], u.im[1][c]);
-            dfacc xi = dfacc_mul(u.re[0][c], u.im[1][d]);
-            dfacc_fma(xi, u.im[0][c], u.re[1][d]);
-            dfacc_fma(xi, -u.re[0][d], u.im[1][c]);
-            dfacc_fma(xi, -u.im[0][d], u.re[1][c]);
-            u.re[2][b] = dfacc_get(xr);
-            u.im[2][b] = -dfacc_get(xi);
+            Acc xr;
+                acc_init(xr);
+                acc_fma(xr, u.re[0][c], u.re[1][d]);
+            acc_fma(xr, -u.im[0][c], u.im[1][d]);
+            acc_fma(xr, -u.re[0][d], u.re[1][c]);
+            acc_fma(xr, u.im[0][d], u.im[1][c]);
+            Acc xi;
+                acc_init(xi);
+                acc_fma(xi, u.re[0][c], u.im[1][d]);
+            acc_fma(xi, u.im[0][c], u.re[1][d]);
+            acc_fma(xi, -u.re[0][d], u.im[1][c]);
+            acc_fma(xi, -u.im[0][d], u.re[1][c]);
+            u.re[2][b] = acc_get(xr);
+            u.im[2][b] = -acc_get(xi);
         }
         return;
     }
@@ -337,7 +350,9 @@ template <typename T> __device__ __forceinline__ void m3_reunitarize(M3<T> &u)
         u.re[1][b] *= n1;
         u.im[1][b] *= n1;
     }
-    m3_rebuild_row2(u);
+    // double-float: the exactly summed products, so that reunitarisation
+    // restores unitarity to the type's own precision
+    m3_rebuild_row2<dfacc>(u);
 }
 
 template <typename T> __device__ __forceinline__ void reunitarize_link(M3<T> &u) { m3_reunitarize(u); }
@@ -442,32 +457,39 @@ __device__ __forceinline__ void su2_or_step(T a0, T a1, T a2, T a3, T omega, int
 }
 
 // rows i, j of m  <-  R rows, R = [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]]
-template <typename T, int I, int J> __device__ __forceinline__ void rotate_rows(M3<T> &m, const T q[4])
+// (double-float: Acc = dfacc for any m, dfsum1 when m is unitary)
+template <typename T, int I, int J, class Acc = dfacc>
+__device__ __forceinline__ void rotate_rows(M3<T> &m, const T q[4])
 {
     if constexpr (std::is_same<T, dfl>::value) {
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             const dfl xr = m.re[I][c], xi = m.im[I][c], yr = m.re[J][c], yi = m.im[J][c];
-            dfacc a = dfacc_mul(q[0], xr);
-            dfacc_fma(a, -q[3], xi);
-            dfacc_fma(a, q[2], yr);
-            dfacc_fma(a, -q[1], yi);
-            dfacc b = dfacc_mul(q[0], xi);
-            dfacc_fma(b, q[3], xr);
-            dfacc_fma(b, q[2], yi);
-            dfacc_fma(b, q[1], yr);
-            dfacc e = dfacc_mul(q[0], yr);
-            dfacc_fma(e, q[3], yi);
-            dfacc_fma(e, -q[2], xr);
-            dfacc_fma(e, -q[1], xi);
-            dfacc f = dfacc_mul(q[0], yi);
-            dfacc_fma(f, -q[3], yr);
-            dfacc_fma(f, -q[2], xi);
-            dfacc_fma(f, q[1], xr);
-            m.re[I][c] = dfacc_get(a);
-            m.im[I][c] = dfacc_get(b);
-            m.re[J][c] = dfacc_get(e);
-            m.im[J][c] = dfacc_get(f);
+            Acc a, b, e, f;
+            acc_init(a);
+            acc_fma(a, q[0], xr);
+            acc_fma(a, -q[3], xi);
+            acc_fma(a, q[2], yr);
+            acc_fma(a, -q[1], yi);
+            acc_init(b);
+            acc_fma(b, q[0], xi);
+            acc_fma(b, q[3], xr);
+            acc_fma(b, q[2], yi);
+            acc_fma(b, q[1], yr);
+            acc_init(e);
+            acc_fma(e, q[0], yr);
+            acc_fma(e, q[3], yi);
+            acc_fma(e, -q[2], xr);
+            acc_fma(e, -q[1], xi);
+            acc_init(f);
+            acc_fma(f, q[0], yi);
+            acc_fma(f, -q[3], yr);
+            acc_fma(f, -q[2], xi);
+            acc_fma(f, q[1], xr);
+            m.re[I][c] = acc_get(a);
+            m.im[I][c] = acc_get(b);
+            m.re[J][c] = acc_get(e);
+            m.im[J][c] = acc_get(f);
         }
         return;
     }
@@ -561,7 +583,7 @@ __device__ __forceinline__ void su3_local_gauge_step(M3<T> &K, M3<T> &g, const S
 
     block_quaternion<T, 1, 2>(K, a0, a1, a2, a3);
     step(a0, a1, a2, a3, 2, q);
-    rotate_rows<T, 1, 2>(g, q);
+    rotate_rows<T, 1, 2, dfsum1>(g, q);
 }
 
 template <typename T> __device__ __forceinline__ void su3_local_gauge(M3<T> &K, M3<T> &g, T omega, int variant)

@@ -167,6 +167,65 @@ __device__ __forceinline__ dfl dfacc_get(const dfacc &r)
     return o;
 }
 
+// Sums of products whose absolute values add up to at most one: the entries
+// of a product of two unitary matrices (sum_k |a_ik| |b_kj| <= 1 by
+// Cauchy-Schwarz) and of the cross product of two orthonormal rows. The
+// leading products are summed onto the constant 2, so every partial sum S
+// lies in [1, 3], on the grid of 2^-23 or 2^-22, and the difference of two
+// of them is an exact float. Each term is then one fused step
+// t = fl(S + a_hi b_hi), whose rounding error S + a_hi b_hi - t is formed by a
+// second FMA as fl(a_hi b_hi + (S - t)) (at most 2^-23 in magnitude, so its
+// own rounding is at most 2^-47); e collects those errors and the cross
+// products hi*lo and lo*hi. Six float operations a term against twelve for
+// dfacc; the result carries an absolute error of a few 2^-47 (dfacc:
+// 2^-48 of the summed magnitudes), ample for links whose entries are at
+// most one. Operands that break the bound (entries above one) still give a
+// sum, with the grid's absolute error.
+struct dfsum1 {
+    float S, e;
+};
+
+__device__ __forceinline__ dfsum1 dfsum1_start()
+{
+    dfsum1 r;
+    r.S = 2.0f;
+    r.e = 0.0f;
+    return r;
+}
+
+// r += a b
+__device__ __forceinline__ void dfsum1_fma(dfsum1 &r, dfl a, dfl b)
+{
+    const float t = fmaf(a.hi, b.hi, r.S);
+    const float d = r.S - t;
+    r.e += fmaf(a.hi, b.hi, d);
+    r.e = fmaf(a.hi, b.lo, r.e);
+    r.e = fmaf(a.lo, b.hi, r.e);
+    r.S = t;
+}
+
+__device__ __forceinline__ dfl dfsum1_get(const dfsum1 &r)
+{
+    dfl o;
+    two_sum(r.S - 2.0f, r.e, o.hi, o.lo);
+    return o;
+}
+
+// One interface over both accumulators, for code templated on the choice:
+// dfsum1 for the link updates (reunitarised every few sweeps), dfacc where
+// a product is multiplied into itself sweep after sweep with nothing to
+// restore it (the accumulated gauge transformation).
+__device__ __forceinline__ void acc_init(dfacc &r)
+{
+    r.s = 0.0f;
+    r.e = 0.0f;
+}
+__device__ __forceinline__ void acc_init(dfsum1 &r) { r = dfsum1_start(); }
+__device__ __forceinline__ void acc_fma(dfacc &r, dfl a, dfl b) { dfacc_fma(r, a, b); }
+__device__ __forceinline__ void acc_fma(dfsum1 &r, dfl a, dfl b) { dfsum1_fma(r, a, b); }
+__device__ __forceinline__ dfl acc_get(const dfacc &r) { return dfacc_get(r); }
+__device__ __forceinline__ dfl acc_get(const dfsum1 &r) { return dfsum1_get(r); }
+
 // a + b without the final renormalisation, for long runs of additions (the
 // gathered K): hi is the exact two-sum of the high parts, lo collects its
 // error and both low parts (a few ulp(hi) after many additions);

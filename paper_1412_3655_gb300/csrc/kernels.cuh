@@ -136,12 +136,12 @@ __device__ __forceinline__ void su3_update(typename P::Chunk *base, const Geom &
             if (mu < mu_first || !valid) continue;
             C *fp = base + plane_offset(g, p, mu, P::NCHUNK) + cb;
             C *bp = base + plane_offset(g, p ^ 1, mu, P::NCHUNK) + cb_shift(g, x, mu, -1);
-            M3<T> u, t;
+            M3<T> u, v, t;
             P::load(fp, g.stride, u);
+            P::load(bp, g.stride, v);
             apply_left<P>(t, G, u);
             P::store(fp, g.stride, t);
-            P::load(bp, g.stride, u);
-            apply_right_adj<P>(t, u, G);
+            apply_right_adj<P>(t, v, G);
             P::store(bp, g.stride, t);
         }
     } else if constexpr (!KEEP && P::NREAL == 18) {
@@ -254,7 +254,7 @@ __device__ __forceinline__ void accumulate_gauge(typename PG::Chunk *gacc, const
         typename PG::Chunk *gp = gacc + (size_t)parity * PG::NCHUNK * g.stride + cb;
         M3<T> a, b;
         PG::load(gp, g.stride, a);
-        m3_mul_rows<0, 1>(b, G, a);
+        m3_mul_rows<0, 1, dfacc>(b, G, a);
         PG::store(gp, g.stride, b);
     }
 }

@@ -177,13 +177,13 @@ template <typename T, class Step> __device__ __forceinline__ void mag_su3_gauge(
     T q[4];
     m3_identity(g);
     mag_block_step<T, 0, 1>(X, step, 0, q);
-    rotate_rows<T, 0, 1>(g, q);
+    rotate_rows<T, 0, 1, dfsum1>(g, q);
     mag_rotate_all<T, 0, 1>(X, q);
     mag_block_step<T, 0, 2>(X, step, 1, q);
-    rotate_rows<T, 0, 2>(g, q);
+    rotate_rows<T, 0, 2, dfsum1>(g, q);
     mag_rotate_all<T, 0, 2>(X, q);
     mag_block_step<T, 1, 2>(X, step, 2, q);
-    rotate_rows<T, 1, 2>(g, q);
+    rotate_rows<T, 1, 2, dfsum1>(g, q);
 }
 
 // the three X_a of site (cb, p) over mu >= 0 (hermitian, both triangles)

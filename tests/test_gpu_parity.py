@@ -96,8 +96,9 @@ def test_one_sweep_fp32(cu, orc, dims, nc):
 
 @pytest.mark.parametrize("dims,nc", CASES)
 def test_one_sweep_double_float(cu, orc, dims, nc):
-    """Double-float sweeps (pairs of floats, unit roundoff 2^-48, 32 times
-    FP64's): one sweep within 32 x the FP64 bound, 3.2e-12."""
+    """Double-float sweeps (pairs of floats, unit roundoff 2^-48; products of
+    unitary factors to a few 2^-47 absolute): one sweep within 32 x the FP64
+    bound, 3.2e-12."""
     U0 = synth.gauge_config(dims, nc, 0.3, 2)
     for U, good in [(U0, False), (warmed(U0, dims, nc, orc), True)]:
         d = to_dev(U)
