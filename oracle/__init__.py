@@ -80,14 +80,16 @@ def _load():
         "oracle_mag_heatbath_sweep": (None, [dp, ip, i, d, u32p, ctypes.c_uint32]),
         "oracle_mag_anneal": (None, [dp, ip, i, d, d, i, i, u32p, i]),
         "oracle_mag_heatbath_su2": (None, [dp, d, u32p, ctypes.c_uint32, ctypes.c_uint32, i, dp]),
-        "oracle_sweep_bound": (None, [dp, ip, i, d, i, d, dp]),
+        "oracle_sweep_bound": (None, [dp, ip, i, d, i, d, dp, i]),
         "oracle_local_gauge_bound": (d, [dp, i, d, i]),
         "oracle_hb_slack": (d, [d, d, d, u32p, ctypes.c_uint32, ctypes.c_uint32, i]),
         "oracle_heatbath_gauge_bound": (d, [dp, i, d, u32p, ctypes.c_uint32, ctypes.c_uint32, d, dp]),
         "oracle_mag_local_gauge_bound": (d, [dp, i, d, i]),
-        "oracle_mag_sweep_bound": (None, [dp, ip, i, d, i, d, dp]),
-        "oracle_heatbath_sweep_bound": (None, [dp, ip, i, d, u32p, ctypes.c_uint32, d, dp, dp]),
-        "oracle_mag_heatbath_sweep_bound": (None, [dp, ip, i, d, u32p, ctypes.c_uint32, d, dp]),
+        "oracle_mag_sweep_bound": (None, [dp, ip, i, d, i, d, dp, i]),
+        "oracle_heatbath_sweep_bound": (None, [dp, ip, i, d, u32p, ctypes.c_uint32, d, dp, dp, i]),
+        "oracle_mag_heatbath_sweep_bound": (None, [dp, ip, i, d, u32p, ctypes.c_uint32, d, dp, i]),
+        "oracle_tangent_bound": (d, [dp, i, i, d, i, d, u32p, ctypes.c_uint32, ctypes.c_uint32]),
+        "oracle_mag_heatbath_gauge": (None, [dp, i, d, u32p, ctypes.c_uint32, ctypes.c_uint32, dp]),
         "oracle_set_threads": (None, [i]),
         "oracle_get_threads": (i, []),
     }
@@ -389,26 +391,29 @@ def _bound_array(e, V):
     return e
 
 
-def sweep_bound(U, L, nc, omega, variant=0, e=None, rho=1.0):
+def sweep_bound(U, L, nc, omega, variant=0, e=None, rho=1.0, tight=False):
     """One overrelaxation sweep, in place, exactly as sweep(); returns the
     first-order bound (V, 4) on how far each output link can move when every
     input link carries the error in e (default: one unit each) and every
-    rounding step of the sweep is charged rho units."""
+    rounding step of the sweep is charged rho units. tight: each SU(3) site's
+    g is also bounded through its exact tangent map (tangent_bound), and the
+    smaller bound kept (slower)."""
     _check_links(U, L, nc)
     e = _bound_array(e, U.shape[0])
-    _load().oracle_sweep_bound(_dp(U), _dims(L), nc, float(omega), int(variant), float(rho), _dp(e))
+    _load().oracle_sweep_bound(_dp(U), _dims(L), nc, float(omega), int(variant), float(rho), _dp(e), int(tight))
     return e
 
 
-def mag_sweep_bound(U, L, nc, omega, variant=0, e=None, rho=1.0):
+def mag_sweep_bound(U, L, nc, omega, variant=0, e=None, rho=1.0, tight=False):
     """One MAG sweep, in place, with the bounds of sweep_bound."""
     _check_links(U, L, nc)
     e = _bound_array(e, U.shape[0])
-    _load().oracle_mag_sweep_bound(_dp(U), _dims(L), nc, float(omega), int(variant), float(rho), _dp(e))
+    _load().oracle_mag_sweep_bound(_dp(U), _dims(L), nc, float(omega), int(variant), float(rho), _dp(e),
+                                   int(tight))
     return e
 
 
-def heatbath_sweep_bound(U, L, nc, T, seed, sweep, e=None, rho=1.0):
+def heatbath_sweep_bound(U, L, nc, T, seed, sweep, e=None, rho=1.0, tight=False):
     """One heat-bath sweep, in place, exactly as heatbath_sweep(); returns
     (e, slack): the bounds of sweep_bound and, per site, the smallest slack
     of its draws' decisions (margin over its own error bound, in units of
@@ -418,16 +423,16 @@ def heatbath_sweep_bound(U, L, nc, T, seed, sweep, e=None, rho=1.0):
     e = _bound_array(e, U.shape[0])
     slack = np.full(U.shape[0], np.inf)
     _load().oracle_heatbath_sweep_bound(_dp(U), _dims(L), nc, float(T), _key(seed), int(sweep), float(rho),
-                                        _dp(e), _dp(slack))
+                                        _dp(e), _dp(slack), int(tight))
     return e, slack
 
 
-def mag_heatbath_sweep_bound(U, L, nc, T, seed, sweep, e=None, rho=1.0):
+def mag_heatbath_sweep_bound(U, L, nc, T, seed, sweep, e=None, rho=1.0, tight=False):
     """One MAG heat-bath sweep, in place, with the bounds of sweep_bound."""
     _check_links(U, L, nc)
     e = _bound_array(e, U.shape[0])
     _load().oracle_mag_heatbath_sweep_bound(_dp(U), _dims(L), nc, float(T), _key(seed), int(sweep), float(rho),
-                                            _dp(e))
+                                            _dp(e), int(tight))
     return e
 
 
@@ -435,6 +440,25 @@ def local_gauge_bound(K, omega, variant=0):
     """First-order bound on ||dg|| per unit ||dK|| for the site transformation of K."""
     K = np.ascontiguousarray(K, dtype=np.complex128)
     return float(_load().oracle_local_gauge_bound(_dp(K), K.shape[0], float(omega), int(variant)))
+
+
+def tangent_bound(inp, mag=False, hb=False, omega=1.7, variant=0, T=1.0, seed=0, site=0, sweep=0):
+    """The tangent bound of one SU(3) site transformation, without rounding:
+    ||dg|| per unit ||dK|| (inp = K, 3 x 3) or per unit max_a ||dX_a||
+    (mag, inp = X, 3 x 3 x 3); overrelaxation, or the heat bath at T with
+    the draws of (seed, site, sweep)."""
+    inp = np.ascontiguousarray(inp, dtype=np.complex128)
+    return float(_load().oracle_tangent_bound(_dp(inp), int(mag), int(hb), float(omega), int(variant), float(T),
+                                              _key(seed), int(site), int(sweep)))
+
+
+def mag_heatbath_gauge(X, T, seed, site, sweep):
+    """The MAG heat-bath transformation g of one site with gathered X_a."""
+    X = np.ascontiguousarray(X, dtype=np.complex128).copy()
+    nc = X.shape[-1]
+    g = np.zeros((nc, nc), dtype=np.complex128)
+    _load().oracle_mag_heatbath_gauge(_dp(X), nc, float(T), _key(seed), int(site), int(sweep), _dp(g))
+    return g
 
 
 def mag_local_gauge_bound(X, omega, variant=0):

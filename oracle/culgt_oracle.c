@@ -264,7 +264,21 @@ typedef struct {
     double *e;     /* per link, V x 4: bound on ||dU_mu(x)||, updated in place */
     double *slack; /* per site, or NULL: smallest decision slack of the heat bath */
     double rho;    /* charge per rounding step */
+    int tight;     /* 1: an SU(3) site's g also takes the tangent bound (tangent_dg) */
 } bound_ctx;
+
+/* The site maps the tangent bound distinguishes: Landau (the running matrix
+ * is K) or MAG (the three X_a), each by overrelaxation or heat bath. */
+typedef struct {
+    int mag, hb;
+    double omega;
+    int variant;
+    double inv_T; /* heat bath */
+    const uint32_t *key;
+    uint32_t site, sweep;
+} site_map;
+
+static double tangent_dg(const site_map *m, const mat *state, double E, double rho);
 
 typedef struct {
     double E;     /* bound on the error of the running K (Landau) or of each X_a (MAG) */
@@ -491,7 +505,12 @@ static void update_site_b(double *U, const lattice *lat, int nc, long i, int mu_
     mat K = gather_K(U, lat, nc, i, mu_first);
     bound_track bt;
     if (bc) bt = track_begin(bc, lat, i, mu_first, 1.0);
+    double E0 = bc ? bt.E : 0.0;
     mat g = local_gauge_b(&K, omega, variant, bc ? &bt : NULL);
+    if (bc && bc->tight && nc == 3) {
+        site_map m = {0, 0, omega, variant, 0.0, NULL, 0, 0};
+        bt.dg = fmin(bt.dg, tangent_dg(&m, &K, E0, bc->rho));
+    }
     mat gd = mat_adj(&g);
     for (int mu = mu_first; mu < 4; mu++) {
         long ib = site_shift(lat, i, mu, -1);
@@ -547,11 +566,12 @@ void oracle_sweep(double *U, const int *L, int nc, double omega, int variant, in
 /* One sweep, exactly as oracle_sweep, carrying the first-order error bounds
  * along: e (V x 4) holds a bound on each input link's error on entry and on
  * each output link's on return, in units of rho (the charge per rounding
- * step; rho = 0 propagates the input errors alone). */
-void oracle_sweep_bound(double *U, const int *L, int nc, double omega, int variant, double rho, double *e)
+ * step; rho = 0 propagates the input errors alone). tight = 1 bounds each
+ * SU(3) site's g also by its tangent map (tangent_dg) and keeps the smaller. */
+void oracle_sweep_bound(double *U, const int *L, int nc, double omega, int variant, double rho, double *e, int tight)
 {
     lattice lat = make_lattice(L);
-    bound_ctx bc = {e, NULL, rho};
+    bound_ctx bc = {e, NULL, rho, tight};
     for (int parity = 0; parity < 2; parity++) {
 #pragma omp parallel for schedule(static)
         for (long i = 0; i < lat.V; i++)
@@ -1172,7 +1192,12 @@ static void heatbath_site_b(double *U, const lattice *lat, int nc, long i, int m
     mat K = gather_K(U, lat, nc, i, mu_first);
     bound_track bt;
     if (bc) bt = track_begin(bc, lat, i, mu_first, 1.0);
+    double E0 = bc ? bt.E : 0.0;
     mat g = heatbath_gauge(&K, inv_T, key, (uint32_t)i, sweep, bc ? &bt : NULL);
+    if (bc && bc->tight && nc == 3) {
+        site_map m = {0, 1, 0.0, 0, inv_T, key, (uint32_t)i, sweep};
+        bt.dg = fmin(bt.dg, tangent_dg(&m, &K, E0, bc->rho));
+    }
     mat gd = mat_adj(&g);
     for (int mu = mu_first; mu < 4; mu++) {
         long ib = site_shift(lat, i, mu, -1);
@@ -1221,10 +1246,10 @@ void oracle_heatbath_sweep(double *U, const int *L, int nc, double T, const uint
  * bounds of oracle_sweep_bound in e (V x 4) and each site's smallest
  * decision slack in slack (V). */
 void oracle_heatbath_sweep_bound(double *U, const int *L, int nc, double T, const uint32_t *key, uint32_t sweep,
-                                 double rho, double *e, double *slack)
+                                 double rho, double *e, double *slack, int tight)
 {
     lattice lat = make_lattice(L);
-    bound_ctx bc = {e, slack, rho};
+    bound_ctx bc = {e, slack, rho, tight};
     double inv_T = 1.0 / T;
     for (int parity = 0; parity < 2; parity++) {
 #pragma omp parallel for schedule(static)
@@ -1405,7 +1430,13 @@ static void mag_update_site_b(double *U, const lattice *lat, int nc, long i, dou
     mag_X(U, lat, nc, i, X);
     bound_track bt;
     if (bc) bt = track_begin(bc, lat, i, 0, 2.0);
+    double E0 = bc ? bt.E : 0.0;
+    mat X0[3] = {X[0], X[1], X[2]};
     mat g = mag_local_gauge_b(X, nc, omega, variant, bc ? &bt : NULL);
+    if (bc && bc->tight && nc == 3) {
+        site_map m = {1, 0, omega, variant, 0.0, NULL, 0, 0};
+        bt.dg = fmin(bt.dg, tangent_dg(&m, X0, E0, bc->rho));
+    }
     mat gd = mat_adj(&g);
     for (int mu = 0; mu < 4; mu++) {
         long ib = site_shift(lat, i, mu, -1);
@@ -1442,10 +1473,11 @@ void oracle_mag_sweep(double *U, const int *L, int nc, double omega, int variant
 
 /* One MAG sweep, exactly as oracle_mag_sweep, with the error bounds of
  * oracle_sweep_bound. */
-void oracle_mag_sweep_bound(double *U, const int *L, int nc, double omega, int variant, double rho, double *e)
+void oracle_mag_sweep_bound(double *U, const int *L, int nc, double omega, int variant, double rho, double *e,
+                            int tight)
 {
     lattice lat = make_lattice(L);
-    bound_ctx bc = {e, NULL, rho};
+    bound_ctx bc = {e, NULL, rho, tight};
     for (int parity = 0; parity < 2; parity++) {
 #pragma omp parallel for schedule(static)
         for (long i = 0; i < lat.V; i++)
@@ -1633,7 +1665,13 @@ static void mag_heatbath_site_b(double *U, const lattice *lat, int nc, long i, d
     mag_X(U, lat, nc, i, X);
     bound_track bt;
     if (bc) bt = track_begin(bc, lat, i, 0, 2.0);
+    double E0 = bc ? bt.E : 0.0;
+    mat X0[3] = {X[0], X[1], X[2]};
     mat g = mag_heatbath_gauge(X, nc, inv_T, key, (uint32_t)i, sweep, bc ? &bt : NULL);
+    if (bc && bc->tight && nc == 3) {
+        site_map m = {1, 1, 0.0, 0, inv_T, key, (uint32_t)i, sweep};
+        bt.dg = fmin(bt.dg, tangent_dg(&m, X0, E0, bc->rho));
+    }
     mat gd = mat_adj(&g);
     for (int mu = 0; mu < 4; mu++) {
         long ib = site_shift(lat, i, mu, -1);
@@ -1660,10 +1698,10 @@ void oracle_mag_heatbath_halfsweep(double *U, const int *L, int nc, int parity, 
 /* One MAG heat-bath sweep with the error bounds of oracle_sweep_bound (the
  * MAG draw takes no decisions, so there is no slack). */
 void oracle_mag_heatbath_sweep_bound(double *U, const int *L, int nc, double T, const uint32_t *key, uint32_t sweep,
-                                     double rho, double *e)
+                                     double rho, double *e, int tight)
 {
     lattice lat = make_lattice(L);
-    bound_ctx bc = {e, NULL, rho};
+    bound_ctx bc = {e, NULL, rho, tight};
     double inv_T = 1.0 / T;
     for (int parity = 0; parity < 2; parity++) {
 #pragma omp parallel for schedule(static)
@@ -1766,6 +1804,426 @@ void oracle_overrelax(const double *g, double omega, int variant, double *out)
     mat a = get_mat(g, 2, 0);
     mat b = overrelax(&a, omega, variant);
     put_mat(out, 2, 0, &b);
+}
+
+/* ------------------------------------------------------------------ */
+/* tight first-order bounds of an SU(3) site: its tangent map          */
+/* ------------------------------------------------------------------ */
+/* F1-F5 bound each subgroup step by norms and compound the bounds over the
+ * three steps of an SU(3) site, which overstates the first-order response
+ * of g by tens (hundreds and more on the random start). tangent_dg carries
+ * the site's first-order map itself: every unit direction of its input (the
+ * 18 real components of K, or a hermitian basis of each X_a) goes through
+ * the exact derivative of each step (the block maximiser, the
+ * overrelaxation or the draw, the rotation of the running matrix, the
+ * product into g), and the bound is the operator norm of the resulting
+ * linear map onto the tangent space of g. Rounding is charged as in F1-F5,
+ * sqrt2 rho on g per step and rho times the rotated rows (F3; MAG: twice
+ * the rows of X_a) on the running matrix, each charge carried by the exact
+ * map of the steps after it. For the heat bath this covers errors of the
+ * input, not the draw's own rounding, which can move x by thousands of
+ * units where a small cosine multiplies log u2 (R10): comparisons of heat-
+ * bath sweeps with another implementation take the norm bound. It bounds the same first-order quantity as the
+ * norm rules, so the smaller of the two holds. */
+
+static const int SUB3[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+
+/* d/dt det(A + t dA) at t = 0 for 2x2 matrices (real part: real for the
+ * quaternion-type pairs here) */
+static double det2_dir(const mat *A, const mat *dA)
+{
+    cplx t = c_add(c_mul(A->m[1][1], dA->m[0][0]), c_mul(A->m[0][0], dA->m[1][1]));
+    t = c_sub(t, c_add(c_mul(A->m[0][1], dA->m[1][0]), c_mul(A->m[1][0], dA->m[0][1])));
+    return t.re;
+}
+
+/* (A - B s) / n for 2x2 matrices */
+static mat comb2(const mat *A, const mat *B, double s, double n)
+{
+    mat out = mat_zero(2);
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++) out.m[a][b] = c_scale(c_sub(A->m[a][b], c_scale(B->m[a][b], s)), 1.0 / n);
+    return out;
+}
+
+/* derivative of su2_local_max at w along dw, for det P(w) > 0:
+ * r = q^+ / n with q = P(w), n = sqrt(det q), so dr = (dq^+ - r dn) / n */
+static mat su2_max_dir(const mat *w, const mat *dw)
+{
+    mat q = su2_part(w), dq = su2_part(dw);
+    double n = sqrt(fmax(mat_det2(&q).re, 0.0));
+    double dn = 0.5 * det2_dir(&q, &dq) / n;
+    mat qd = mat_adj(&q), dqd = mat_adj(&dq);
+    return comb2(&dqd, &qd, dn / n, n);
+}
+
+/* derivative of mag_su2_max at Z along dZ, for |z| > 0 and z off -e3:
+ * B = M / s with s = sqrt(det M), so dB = (dM - B ds) / s */
+static mat mag_max_dir(const mat *Z, const mat *dZ)
+{
+    double z3 = 0.5 * (Z->m[0][0].re - Z->m[1][1].re), z1 = Z->m[0][1].re, z2 = -Z->m[0][1].im;
+    double d3 = 0.5 * (dZ->m[0][0].re - dZ->m[1][1].re), d1 = dZ->m[0][1].re, d2 = -dZ->m[0][1].im;
+    double n = sqrt(z1 * z1 + z2 * z2 + z3 * z3);
+    double dn = (z1 * d1 + z2 * d2 + z3 * d3) / n;
+    mat M = mat_zero(2), dM = mat_zero(2);
+    M.m[0][0] = M.m[1][1] = c_make(n + z3, 0.0);
+    M.m[0][1] = c_make(z1, -z2);
+    M.m[1][0] = c_make(-z1, -z2);
+    dM.m[0][0] = dM.m[1][1] = c_make(dn + d3, 0.0);
+    dM.m[0][1] = c_make(d1, -d2);
+    dM.m[1][0] = c_make(-d1, -d2);
+    double s = sqrt(mat_det2(&M).re);
+    double ds = 0.5 * det2_dir(&M, &dM) / s;
+    return comb2(&dM, &M, ds / s, s);
+}
+
+/* derivative of overrelax at the SU(2) element r along the tangent dr;
+ * *ok = 0 where the map has none (variant 1 at r = -1) */
+static mat or_dir(const mat *r, const mat *dr, double omega, int variant, int *ok)
+{
+    mat out = mat_zero(2);
+    if (variant == 0) {
+        /* G = 1 + omega D + c D^2 (D = r - 1), out = G / sqrt(det G) */
+        double c = 0.5 * omega * (omega - 1.0);
+        mat one = mat_identity(2);
+        mat D = mat_sub(r, &one);
+        mat D2 = mat_mul(&D, &D);
+        mat t1 = mat_scale(&D, c_make(omega, 0.0)), t2 = mat_scale(&D2, c_make(c, 0.0));
+        mat G = mat_add(&one, &t1);
+        G = mat_add(&G, &t2);
+        mat a1 = mat_mul(dr, &D), a2 = mat_mul(&D, dr);
+        mat dG = mat_add(&a1, &a2);
+        dG = mat_scale(&dG, c_make(c, 0.0));
+        mat o1 = mat_scale(dr, c_make(omega, 0.0));
+        dG = mat_add(&dG, &o1);
+        double m = sqrt(fmax(mat_det2(&G).re, 0.0));
+        if (!(m > 0.0)) {
+            *ok = 0;
+            return out;
+        }
+        double dm = 0.5 * det2_dir(&G, &dG) / m;
+        mat Gm = mat_scale(&G, c_make(1.0 / m, 0.0));
+        return comb2(&dG, &Gm, dm, m);
+    }
+    /* out = cos(omega phi) 1 + f S, S = (r - r^+)/2, f = sin(omega phi) / sin(phi) */
+    mat rd = mat_adj(r);
+    mat S = mat_sub(r, &rd);
+    S = mat_scale(&S, c_make(0.5, 0.0));
+    double cphi = 0.5 * mat_trace(r).re;
+    double sphi = sqrt(fmax(mat_det2(&S).re, 0.0));
+    if (sphi == 0.0) {
+        if (cphi > 0.0) return mat_scale(dr, c_make(omega, 0.0)); /* r^omega at r = 1 */
+        *ok = 0;
+        return out;
+    }
+    double phi = atan2(sphi, cphi);
+    mat drd = mat_adj(dr);
+    mat dS = mat_sub(dr, &drd);
+    dS = mat_scale(&dS, c_make(0.5, 0.0));
+    double dc = 0.5 * mat_trace(dr).re;
+    double ds = 0.5 * det2_dir(&S, &dS) / sphi;
+    double dphi = (cphi * ds - sphi * dc) / (cphi * cphi + sphi * sphi);
+    double f = sin(omega * phi) / sphi;
+    double df = (omega * cos(omega * phi) * dphi - f * ds) / sphi;
+    mat p1 = mat_scale(&dS, c_make(f, 0.0)), p2 = mat_scale(&S, c_make(df, 0.0));
+    out = mat_add(&p1, &p2);
+    double dd = -omega * sin(omega * phi) * dphi;
+    out.m[0][0] = c_add(out.m[0][0], c_make(dd, 0.0));
+    out.m[1][1] = c_add(out.m[1][1], c_make(dd, 0.0));
+    return out;
+}
+
+/* One subgroup step, linearised: the block, the maximiser v (Landau) or
+ * Bmax (MAG), the SU(2) element applied, and for the heat bath the drawn
+ * quaternion X with its derivative per unit alpha (beta) at the same
+ * uniforms, a central difference as in hb_track */
+typedef struct {
+    mat blk, v, r, X;
+    double xp[4];
+    double k; /* Landau: sqrt(det P(w)); MAG: |z| */
+    int ok;
+} step_lin;
+
+/* the 2x2 block of step s: of K (Landau), or of X_i - X_j (MAG) */
+static mat block_of(const site_map *m, const mat *S, int s)
+{
+    int i = SUB3[s][0], j = SUB3[s][1];
+    mat D = m->mag ? mat_sub(&S[i], &S[j]) : S[0];
+    mat w = mat_zero(2);
+    w.m[0][0] = D.m[i][i];
+    w.m[0][1] = D.m[i][j];
+    w.m[1][0] = D.m[j][i];
+    w.m[1][1] = D.m[j][j];
+    return w;
+}
+
+static void lin_step(const site_map *m, const mat *blk, int s, step_lin *L)
+{
+    L->blk = *blk;
+    L->ok = 1;
+    if (!m->mag) {
+        mat q = su2_part(blk);
+        L->k = sqrt(fmax(mat_det2(&q).re, 0.0));
+        if (!(L->k > 0.0)) {
+            L->ok = 0;
+            return;
+        }
+        L->v = su2_local_max(blk);
+        if (!m->hb) {
+            L->r = overrelax(&L->v, m->omega, m->variant);
+            return;
+        }
+        L->r = heatbath_su2(blk, m->inv_T, m->key, m->site, m->sweep, s, NULL, 0.0);
+        double alpha = (2.0 * L->k) * m->inv_T, h = FD_STEP * alpha, x[4], xa[4], xb[4];
+        oracle_hb_x(alpha, m->key, m->site, m->sweep, s, x);
+        oracle_hb_x(alpha + h, m->key, m->site, m->sweep, s, xa);
+        oracle_hb_x(alpha - h, m->key, m->site, m->sweep, s, xb);
+        for (int c = 0; c < 4; c++) L->xp[c] = (xa[c] - xb[c]) / (2.0 * h);
+        L->X = quaternion_matrix(x);
+        return;
+    }
+    double z3 = 0.5 * (blk->m[0][0].re - blk->m[1][1].re), z1 = blk->m[0][1].re, z2 = -blk->m[0][1].im;
+    L->k = sqrt(z1 * z1 + z2 * z2 + z3 * z3);
+    if (!(L->k > 0.0) || !(L->k + z3 > 0.0)) {
+        L->ok = 0;
+        return;
+    }
+    L->v = mag_su2_max(blk);
+    if (!m->hb) {
+        L->r = overrelax(&L->v, m->omega, m->variant);
+        return;
+    }
+    L->r = mag_heatbath_su2(blk, m->inv_T, m->key, m->site, m->sweep, s, NULL, 0.0, 0.0);
+    double beta = (2.0 * L->k) * m->inv_T, h = FD_STEP * beta, v[4], u, w, up, wp, um, wm;
+    draw4(m->key, m->site, m->sweep, (uint32_t)s << 1, v);
+    mag_hb_uw(beta, v[0], &u, &w);
+    mag_hb_uw(beta + h, v[0], &up, &wp);
+    mag_hb_uw(beta - h, v[0], &um, &wm);
+    double a = (sqrt(fmax(up, 0.0)) - sqrt(fmax(um, 0.0))) / (2.0 * h);
+    double b = (sqrt(fmax(wp, 0.0)) - sqrt(fmax(wm, 0.0))) / (2.0 * h);
+    double ca = cos(TWO_PI * v[1]), sa = sin(TWO_PI * v[1]), cc = cos(TWO_PI * v[2]), sc = sin(TWO_PI * v[2]);
+    double c[4] = {sqrt(u) * ca, sqrt(w) * cc, sqrt(w) * sc, sqrt(u) * sa};
+    L->X = quaternion_matrix(c);
+    L->xp[0] = a * ca;
+    L->xp[1] = b * cc;
+    L->xp[2] = b * sc;
+    L->xp[3] = a * sa;
+}
+
+/* the step's SU(2) element moved along the block's tangent dblk */
+static mat step_dr(const site_map *m, const step_lin *L, const mat *dblk, int *ok)
+{
+    mat dv = m->mag ? mag_max_dir(&L->blk, dblk) : su2_max_dir(&L->blk, dblk);
+    if (!m->hb) return or_dir(&L->v, &dv, m->omega, m->variant, ok);
+    /* heat bath: r = X v, X moving with alpha = 2 k / T (MAG: beta = 2 |z| / T) */
+    double dk;
+    if (!m->mag) {
+        mat q = su2_part(&L->blk), dq = su2_part(dblk);
+        dk = 0.5 * det2_dir(&q, &dq) / L->k;
+    } else {
+        double z3 = 0.5 * (L->blk.m[0][0].re - L->blk.m[1][1].re), z1 = L->blk.m[0][1].re,
+               z2 = -L->blk.m[0][1].im;
+        double d3 = 0.5 * (dblk->m[0][0].re - dblk->m[1][1].re), d1 = dblk->m[0][1].re, d2 = -dblk->m[0][1].im;
+        dk = (z1 * d1 + z2 * d2 + z3 * d3) / L->k;
+    }
+    double dpar = 2.0 * dk * m->inv_T, dx[4];
+    for (int c = 0; c < 4; c++) dx[c] = L->xp[c] * dpar;
+    mat dX = quaternion_matrix(dx);
+    mat t1 = mat_mul(&dX, &L->v), t2 = mat_mul(&L->X, &dv);
+    return mat_add(&t1, &t2);
+}
+
+/* 3x3 with the 2x2 block b at rows/columns i, j; `one` = 1 elsewhere on the diagonal, else 0 */
+static mat embed3(const mat *b, int i, int j, int one)
+{
+    mat R = one ? mat_identity(3) : mat_zero(3);
+    R.m[i][i] = b->m[0][0];
+    R.m[i][j] = b->m[0][1];
+    R.m[j][i] = b->m[1][0];
+    R.m[j][j] = b->m[1][1];
+    return R;
+}
+
+/* coordinates of an element of su(3) (anti-hermitian, traceless) in an
+ * orthonormal basis: sqrt2 Re, Im of the entries above the diagonal and two
+ * combinations of the diagonal's imaginary parts; their Euclidean norm is
+ * the Frobenius norm */
+static void su3_coords(const mat *X, double *c)
+{
+    c[0] = SQRT2 * X->m[0][1].re;
+    c[1] = SQRT2 * X->m[0][1].im;
+    c[2] = SQRT2 * X->m[0][2].re;
+    c[3] = SQRT2 * X->m[0][2].im;
+    c[4] = SQRT2 * X->m[1][2].re;
+    c[5] = SQRT2 * X->m[1][2].im;
+    c[6] = (X->m[0][0].im - X->m[1][1].im) / SQRT2;
+    c[7] = (X->m[0][0].im + X->m[1][1].im - 2.0 * X->m[2][2].im) / sqrt(6.0);
+}
+
+/* ||J||_2 from above for the 8 x n matrix J (column c at J + 8 c): for the
+ * symmetric M = J J^T >= 0, lambda_max^16 <= tr M^16 <= 8 lambda_max^16, so
+ * (tr M^16)^(1/32) is at most 8^(1/32) = 1.067 times ||J||_2. M^16 by four
+ * squarings, each renormalised to unit trace, the traces kept as logs. */
+static double opnorm8(const double *J, int n)
+{
+    double M[8][8], T[8][8];
+    for (int a = 0; a < 8; a++)
+        for (int b = 0; b < 8; b++) {
+            double s = 0.0;
+            for (int c = 0; c < n; c++) s += J[8 * c + a] * J[8 * c + b];
+            M[a][b] = s;
+        }
+    double t = 0.0;
+    for (int a = 0; a < 8; a++) t += M[a][a];
+    if (!(t > 0.0)) return t == 0.0 ? 0.0 : INFINITY;
+    double lg = 16.0 * log(t), p = 8.0;
+    for (int a = 0; a < 8; a++)
+        for (int b = 0; b < 8; b++) M[a][b] /= t;
+    for (int k = 0; k < 4; k++) {
+        t = 0.0;
+        for (int a = 0; a < 8; a++)
+            for (int b = 0; b < 8; b++) {
+                double s = 0.0;
+                for (int c = 0; c < 8; c++) s += M[a][c] * M[c][b];
+                T[a][b] = s;
+            }
+        for (int a = 0; a < 8; a++) t += T[a][a];
+        for (int a = 0; a < 8; a++)
+            for (int b = 0; b < 8; b++) M[a][b] = T[a][b] / t;
+        lg += p * log(t);
+        p *= 0.5;
+    }
+    return exp(lg / 32.0);
+}
+
+/* unit direction d of the site's input: K (18 real components), or the
+ * hermitian basis of each X_a (9 per a: diagonal units, then the symmetric
+ * and antisymmetric pairs of each entry above the diagonal over sqrt2) */
+static void unit_dir(const site_map *m, int d, mat *dS)
+{
+    for (int a = 0; a < 3; a++) dS[a] = mat_zero(3);
+    if (!m->mag) {
+        int e = d / 2;
+        dS[0].m[e / 3][e % 3] = (d & 1) ? c_make(0.0, 1.0) : c_make(1.0, 0.0);
+        return;
+    }
+    int a = d / 9, e = d % 9;
+    if (e < 3) {
+        dS[a].m[e][e] = c_make(1.0, 0.0);
+        return;
+    }
+    static const int pr[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    int k = pr[(e - 3) / 2][0], l = pr[(e - 3) / 2][1];
+    if ((e - 3) % 2 == 0) {
+        dS[a].m[k][l] = c_make(1.0 / SQRT2, 0.0);
+        dS[a].m[l][k] = c_make(1.0 / SQRT2, 0.0);
+    } else {
+        dS[a].m[k][l] = c_make(0.0, 1.0 / SQRT2);
+        dS[a].m[l][k] = c_make(0.0, -1.0 / SQRT2);
+    }
+}
+
+/* Operator norm (from above) of the map from the running input at step s0
+ * to the tangent of g through steps s0..2: Landau ||J||, MAG the sum over a
+ * of ||J_a|| (per unit max_a ||dX_a||). S[s] are the running inputs, L[s]
+ * the steps, R[s] their 3x3 rotations. */
+static double tail_norm(const site_map *m, mat S[4][3], const step_lin *L, const mat *R, int s0)
+{
+    if (s0 == 3) return 0.0;
+    int nin = m->mag ? 27 : 18;
+    double J[27 * 8];
+    for (int d = 0; d < nin; d++) {
+        mat dS[3];
+        unit_dir(m, d, dS);
+        mat dg = mat_zero(3), gt = mat_identity(3);
+        for (int s = s0; s < 3; s++) {
+            int i = SUB3[s][0], j = SUB3[s][1], ok = 1;
+            mat dblk = block_of(m, dS, s);
+            mat dr = step_dr(m, &L[s], &dblk, &ok);
+            if (!ok) return INFINITY;
+            mat dR = embed3(&dr, i, j, 0);
+            if (!m->mag) {
+                mat t1 = mat_mul(&dR, &S[s][0]), t2 = mat_mul(&R[s], &dS[0]);
+                dS[0] = mat_add(&t1, &t2);
+            } else {
+                /* X_a' = R X_a R^+: dX_a' = Y + Y^+ + R dX_a R^+, Y = dR X_a R^+ */
+                mat Rd = mat_adj(&R[s]);
+                for (int a = 0; a < 3; a++) {
+                    mat P = mat_mul(&S[s][a], &Rd);
+                    mat Y = mat_mul(&dR, &P);
+                    mat Yd = mat_adj(&Y);
+                    mat t = mat_mul(&R[s], &dS[a]);
+                    mat Q = mat_mul(&t, &Rd);
+                    dS[a] = mat_add(&Y, &Yd);
+                    dS[a] = mat_add(&dS[a], &Q);
+                }
+            }
+            mat t1 = mat_mul(&dR, &gt), t2 = mat_mul(&R[s], &dg);
+            dg = mat_add(&t1, &t2);
+            gt = mat_mul(&R[s], &gt);
+        }
+        mat gtd = mat_adj(&gt);
+        mat X = mat_mul(&dg, &gtd);
+        su3_coords(&X, J + 8 * d);
+    }
+    if (!m->mag) return opnorm8(J, 18);
+    return opnorm8(J, 9) + opnorm8(J + 72, 9) + opnorm8(J + 144, 9);
+}
+
+/* The tangent bound on ||dg|| of an SU(3) site whose input (K, or the X_a)
+ * is known to within E, with rho per rounding step. */
+static double tangent_dg(const site_map *m, const mat *state, double E, double rho)
+{
+    mat S[4][3];
+    step_lin L[3];
+    mat R[3];
+    double rr[3], amp[4];
+    int ns = m->mag ? 3 : 1;
+    for (int a = 0; a < ns; a++) S[0][a] = state[a];
+    for (int s = 0; s < 3; s++) {
+        int i = SUB3[s][0], j = SUB3[s][1];
+        mat blk = block_of(m, S[s], s);
+        lin_step(m, &blk, s, &L[s]);
+        if (!L[s].ok) return INFINITY;
+        R[s] = embed3(&L[s].r, i, j, 1);
+        rr[s] = m->mag ? mag_rows(S[s], 3, i, j, 0) : rows_norm(&S[s][0], i, j);
+        if (!m->mag) {
+            S[s + 1][0] = mat_mul(&R[s], &S[s][0]);
+        } else {
+            mat Rd = mat_adj(&R[s]);
+            for (int a = 0; a < 3; a++) {
+                mat t = mat_mul(&R[s], &S[s][a]);
+                S[s + 1][a] = mat_mul(&t, &Rd);
+            }
+        }
+    }
+    for (int s0 = 0; s0 <= 3; s0++) amp[s0] = tail_norm(m, S, L, R, s0);
+    double dg = amp[0] * E;
+    for (int s = 0; s < 3; s++) dg += SQRT2 * rho + amp[s + 1] * rr[s] * rho;
+    return dg;
+}
+
+/* The tangent bound of one SU(3) site map with no rounding: ||dg|| per unit
+ * ||dK|| (mag = 0; in = K) or per unit max_a ||dX_a|| (mag = 1; in = X_0..2),
+ * for overrelaxation (hb = 0) or the heat bath at T (hb = 1, draws of
+ * (key, site, sweep)). */
+double oracle_tangent_bound(const double *in, int mag, int hb, double omega, int variant, double T,
+                            const uint32_t *key, uint32_t site, uint32_t sweep)
+{
+    mat S[3];
+    for (int a = 0; a < (mag ? 3 : 1); a++) S[a] = get_mat(in, 3, a);
+    site_map m = {mag, hb, omega, variant, hb ? 1.0 / T : 0.0, key, site, sweep};
+    return tangent_dg(&m, S, 1.0, 0.0);
+}
+
+/* The MAG heat-bath site transformation of the X_a (consumed) into g. */
+void oracle_mag_heatbath_gauge(double *X, int nc, double T, const uint32_t *key, uint32_t site, uint32_t sweep,
+                               double *g)
+{
+    mat Xm[3];
+    for (int a = 0; a < nc; a++) Xm[a] = get_mat(X, nc, a);
+    mat G = mag_heatbath_gauge(Xm, nc, 1.0 / T, key, site, sweep, NULL);
+    put_mat(g, nc, 0, &G);
 }
 
 void oracle_set_threads(int n)

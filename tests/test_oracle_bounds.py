@@ -333,3 +333,153 @@ def test_mag_local_bound_holds(orc, nc):
             dX /= np.linalg.norm(dX.reshape(nc, -1), axis=1).max()
             g1 = orc.mag_local_gauge(X + h * dX, 1.7)[0]
             assert np.linalg.norm(g1 - g0) / h <= B * (1 + 1e-3)
+
+
+# --- the tangent bound of an SU(3) site (tight = True) ---
+
+TRACE_POWER = 8 ** (1 / 32)  # (tr M^16)^(1/32) over ||J||_2 is at most this for rank <= 8
+
+
+def gathered_X(U, L):
+    """The MAG X_a(x) = sum_mu [U P_a U^+ + U(x-mu)^+ P_a U(x-mu)] for every site, (V, Nc, Nc, Nc)."""
+    nc = U.shape[-1]
+    X = np.zeros((U.shape[0], nc, nc, nc), dtype=complex)
+    for mu in range(4):
+        f = U[:, mu]
+        bk = U[P.shifted(L, mu, -1), mu]
+        for a in range(nc):
+            X[:, a] += np.einsum("vi,vj->vij", f[:, :, a], np.conj(f[:, :, a]))
+            X[:, a] += np.einsum("vi,vj->vij", np.conj(bk[:, a, :]), bk[:, a, :])
+    return X
+
+
+def hermitian_jacobian_norms(f, X, h=1e-7):
+    """Per a, the largest singular value of the Jacobian of f along an
+    orthonormal hermitian basis of X_a (central differences)."""
+    nc = X.shape[-1]
+    out = []
+    for a in range(nc):
+        cols = []
+        for r in range(nc):
+            for c in range(r, nc):
+                for z in ((1.0,) if r == c else (1.0, 1j)):
+                    E = np.zeros(X.shape, dtype=complex)
+                    if r == c:
+                        E[a, r, r] = 1.0
+                    else:
+                        E[a, r, c] = z / np.sqrt(2)
+                        E[a, c, r] = np.conj(z) / np.sqrt(2)
+                    D = (f(X + h * E) - f(X - h * E)) / (2 * h)
+                    cols.append(np.concatenate([D.real.ravel(), D.imag.ravel()]))
+        out.append(np.linalg.svd(np.array(cols).T, compute_uv=False)[0])
+    return out
+
+
+TANGENT_KINDS = ["or", "or_power", "hb", "mag", "mag_power", "mag_hb"]
+
+
+@pytest.mark.parametrize("kind", TANGENT_KINDS)
+@pytest.mark.parametrize("warm", [0, 5])
+def test_tangent_bound_is_the_jacobian_norm(orc, kind, warm):
+    """The tangent bound of an SU(3) site (no rounding) against the exact
+    Jacobian of the oracle's own site transformation by central differences:
+    Landau per unit ||dK||, MAG per unit max_a ||dX_a|| (the sum over a of
+    the hermitian blocks' norms). It is that norm taken from above through
+    a trace power, so it lies within [1, 8^(1/32)] of it; a dropped term or
+    a wrong sign in any step's derivative moves it out."""
+    L = (4, 4, 4, 4)
+    U = synth.gauge_config(L, 3, 0.3, 2)
+    mag = kind.startswith("mag")
+    if warm:
+        (orc.mag_sweep if mag else orc.sweep)(U, L, 3, 1.7, warm)
+    inputs = gathered_X(U, L) if mag else gathered_K(U, L)
+    ratios = []
+    for i in range(0, int(np.prod(L)), 9):
+        M = inputs[i]
+        if kind.endswith("hb"):
+            for T in (0.05, 2.0):
+                B = orc.tangent_bound(M, mag=mag, hb=True, T=T, seed=9, site=i, sweep=4)
+                if mag:
+                    J = sum(hermitian_jacobian_norms(lambda x: orc.mag_heatbath_gauge(x, T, 9, i, 4), M))
+                else:
+                    J = jacobian_norm(lambda k: orc.heatbath_gauge(k, T, 9, i, 4), M)
+                ratios.append(B / J)
+            continue
+        omega, variant = (1.5, 1) if kind.endswith("power") else (1.7, 0)
+        B = orc.tangent_bound(M, mag=mag, omega=omega, variant=variant)
+        if mag:
+            J = sum(hermitian_jacobian_norms(lambda x: orc.mag_local_gauge(x, omega, variant)[0], M))
+        else:
+            J = jacobian_norm(lambda k: orc.local_gauge(k, omega, variant), M)
+        ratios.append(B / J)
+    ratios = np.array(ratios)
+    assert len(ratios) >= 29
+    assert ratios.min() >= 1 - 1e-5 and ratios.max() <= TRACE_POWER + 1e-5, (ratios.min(), ratios.max())
+
+
+def tight_pair(orc, kind, warm):
+    L = (8, 8, 8, 8)
+    U = synth.gauge_config(L, 3, 0.3, 2)
+    if warm:
+        (orc.mag_sweep if kind.startswith("mag") else orc.sweep)(U, L, 3, 1.7, warm)
+    return L, U
+
+
+def run_bound(orc, kind, U, L, tight, e=None, rho=1.0):
+    """One sweep of this kind in place; (bound, slack or None)."""
+    if kind == "or":
+        return orc.sweep_bound(U, L, 3, 1.7, 0, e=e, rho=rho, tight=tight), None
+    if kind == "mag":
+        return orc.mag_sweep_bound(U, L, 3, 1.7, 0, e=e, rho=rho, tight=tight), None
+    if kind == "hb":
+        return orc.heatbath_sweep_bound(U, L, 3, 0.5, 7, 3, e=e, rho=rho, tight=tight)
+    return orc.mag_heatbath_sweep_bound(U, L, 3, 0.5, 7, 3, e=e, rho=rho, tight=tight), None
+
+
+def run_plain(orc, kind, U, L):
+    if kind == "or":
+        orc.sweep(U, L, 3, 1.7, 1)
+    elif kind == "mag":
+        orc.mag_sweep(U, L, 3, 1.7, 1)
+    elif kind == "hb":
+        orc.heatbath_sweep(U, L, 3, 0.5, 7, 3)
+    else:
+        orc.mag_heatbath_sweep(U, L, 3, 0.5, 7, 3)
+
+
+@pytest.mark.parametrize("kind", ["or", "mag", "hb", "mag_hb"])
+@pytest.mark.parametrize("warm", [0, 5])
+def test_tight_sweep_bound_holds_under_perturbation(orc, kind, warm):
+    """SU(3) sweeps with the tangent bound, as for the norm bound: every link
+    of a perturbed input moves by no more than its bound (outside the sites
+    whose heat-bath decisions the perturbation may flip)."""
+    L, U = tight_pair(orc, kind, warm)
+    a, b, e0 = perturbed_pair(U, DELTA, 2)
+    plain = U.copy()
+    run_plain(orc, kind, plain, L)
+    A, slack = run_bound(orc, kind, a, L, True, e=e0, rho=0.0)
+    assert np.array_equal(a, plain)
+    run_plain(orc, kind, b, L)
+    exempt = None
+    if slack is not None:
+        flagged = slack < DELTA
+        black = flagged & (P.parity(L) == 0)
+        spread = black.copy()
+        for mu in range(4):
+            spread |= black[P.shifted(L, mu, 1)] | black[P.shifted(L, mu, -1)]
+        exempt = P.links_touching(L, flagged | spread)
+    assert_bound_holds(A, moved(a, b, DELTA), exempt)
+
+
+@pytest.mark.parametrize("kind", ["or", "mag", "hb", "mag_hb"])
+def test_tight_bound_is_the_smaller(orc, kind):
+    """The tangent bound only replaces a site's norm bound where it is
+    smaller, so no link's bound grows, and the sweep is the same; on the
+    random start it is far smaller (a factor of 10 in the median or more)."""
+    L, U = tight_pair(orc, kind, 0)
+    a, b = U.copy(), U.copy()
+    An, _ = run_bound(orc, kind, a, L, False)
+    At, _ = run_bound(orc, kind, b, L, True)
+    assert np.array_equal(a, b)
+    assert (At <= An).all()
+    assert np.median(An / At) >= 10
