@@ -418,7 +418,10 @@ def heatbath_sweep_bound(U, L, nc, T, seed, sweep, e=None, rho=1.0, tight=False)
     (e, slack): the bounds of sweep_bound and, per site, the smallest slack
     of its draws' decisions (margin over its own error bound, in units of
     the per-step charge): an implementation whose unit roundoff exceeds the
-    slack may take that decision the other way."""
+    slack may take that decision the other way. tight bounds the effect of
+    input errors through the tangent map but charges the draws' own rounding
+    as one step only; comparisons with another implementation take the norm
+    bound."""
     _check_links(U, L, nc)
     e = _bound_array(e, U.shape[0])
     slack = np.full(U.shape[0], np.inf)
