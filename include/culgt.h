@@ -218,6 +218,15 @@ culgt_status culgt_coulomb_fix(void *d_links, const culgt_params *p, void *cuda_
 culgt_status culgt_landau_fix_gauge(void *d_links, const culgt_params *p, void *cuda_stream, culgt_result *out,
                                     void *d_gauge);
 
+/* Maximally Abelian gauge fixing like culgt_mag_fix (p->gauge is taken as
+ * CULGT_MAG), also returning g(x) as culgt_landau_fix_gauge does: on return
+ * d_links = g(x) U_mu(x) g(x+mu)^+ for the input U and d_gauge = g(x) as
+ * [V][Nc][Nc] complex double in canonical site order (the transformation
+ * that diagonalises the links as far as the MAG functional of Sec. 1 asks).
+ * Errors as culgt_mag_fix; d_gauge NULL is CULGT_ERR_ARG. */
+culgt_status culgt_mag_fix_gauge(void *d_links, const culgt_params *p, void *cuda_stream, culgt_result *out,
+                                 void *d_gauge);
+
 /* n_sweeps sweeps of d_links in place at the given precision, for the
  * functional p->gauge names. */
 culgt_status culgt_sweep(void *d_links, const culgt_params *p, int n_sweeps, void *cuda_stream);

@@ -493,13 +493,14 @@ extern "C" culgt_status culgt_fix_batched_anneal(const culgt_problem *problems, 
     return fix_batched(problems, n, common, a, cuda_stream, out);
 }
 
-extern "C" culgt_status culgt_landau_fix_gauge(void *d_links, const culgt_params *p, void *cuda_stream,
-                                               culgt_result *out, void *d_gauge)
+namespace {
+
+// One fix of one lattice in the gauge of p (Landau or MAG) through the
+// engine with g(x) kept in every phase, written to d_gauge in the canonical
+// order; the input is validated by the callers.
+culgt_status fix_gauge_call(void *d_links, const culgt_params *p, void *cuda_stream, culgt_result *out,
+                            void *d_gauge, double t0)
 {
-    double t0 = wall_now();
-    culgt_status st = culgt_validate(p);
-    if (st != CULGT_OK) return st;
-    if (p->gauge != CULGT_LANDAU) return CULGT_ERR_ARG;
     if (!d_links || !d_gauge) return CULGT_ERR_ARG;
     if (cudaStreamSynchronize((cudaStream_t)cuda_stream) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -535,6 +536,29 @@ extern "C" culgt_status culgt_landau_fix_gauge(void *d_links, const culgt_params
         out->seconds = wall_now() - t0;
     }
     return e.status();
+}
+
+} // namespace
+
+extern "C" culgt_status culgt_landau_fix_gauge(void *d_links, const culgt_params *p, void *cuda_stream,
+                                               culgt_result *out, void *d_gauge)
+{
+    double t0 = wall_now();
+    culgt_status st = culgt_validate(p);
+    if (st != CULGT_OK) return st;
+    if (p->gauge != CULGT_LANDAU) return CULGT_ERR_ARG;
+    return fix_gauge_call(d_links, p, cuda_stream, out, d_gauge, t0);
+}
+
+extern "C" culgt_status culgt_mag_fix_gauge(void *d_links, const culgt_params *p, void *cuda_stream,
+                                            culgt_result *out, void *d_gauge)
+{
+    double t0 = wall_now();
+    culgt_status st = culgt_validate(p);
+    if (st != CULGT_OK) return st;
+    culgt_params q = *p;
+    q.gauge = CULGT_MAG;
+    return fix_gauge_call(d_links, &q, cuda_stream, out, d_gauge, t0);
 }
 
 namespace {

@@ -192,6 +192,7 @@ def library():
         "culgt_theta_static_scratch": (ip, [vp, P, vp, vp]),
         "culgt_coulomb_fix": (ip, [vp, P, vp, R, vp]),
         "culgt_landau_fix_gauge": (ip, [vp, P, vp, R, vp]),
+        "culgt_mag_fix_gauge": (ip, [vp, P, vp, R, vp]),
         "culgt_fix_batched": (ip, [ctypes.POINTER(_Problem), ip, P, vp, R]),
         "culgt_reunitarize": (ip, [vp, P, vp]),
         "culgt_default_anneal_params": (ip, [A]),
@@ -314,6 +315,16 @@ def culgt_landau_fix_gauge(links, params: Params, gauge, stream=None) -> Result:
     st = _check(library().culgt_landau_fix_gauge(_links_ptr(links, params, True), ctypes.byref(params._c()),
                                                  _stream(stream), ctypes.byref(r), _gauge_ptr(gauge, params)),
                 "culgt_landau_fix_gauge")
+    return Result._from(r, st)
+
+
+def culgt_mag_fix_gauge(links, params: Params, gauge, stream=None) -> Result:
+    """Maximally Abelian gauge fixing in place that also writes g(x) into
+    `gauge` (CUDA float64/complex128 tensor of V * Nc * Nc complex values)."""
+    r = _Result()
+    st = _check(library().culgt_mag_fix_gauge(_links_ptr(links, params, True), ctypes.byref(params._c()),
+                                              _stream(stream), ctypes.byref(r), _gauge_ptr(gauge, params)),
+                "culgt_mag_fix_gauge")
     return Result._from(r, st)
 
 

@@ -168,6 +168,15 @@ def test_gauge_field_validates(lib):
     assert so.culgt_landau_fix_anneal(ctypes.c_void_p(16), ctypes.byref(q._c()), ctypes.byref(a._c()), None,
                                       None) == lib.ERR_ARG
     assert so.culgt_mag_fix(None, ctypes.byref(q._c()), None, None) == lib.ERR_ARG
+    # the gauge-returning fixes: Landau refuses a MAG block, both refuse null buffers
+    assert so.culgt_landau_fix_gauge(ctypes.c_void_p(16), ctypes.byref(q._c()), None, None,
+                                     ctypes.c_void_p(16)) == lib.ERR_ARG
+    assert so.culgt_mag_fix_gauge(None, ctypes.byref(q._c()), None, None, ctypes.c_void_p(16)) == lib.ERR_ARG
+    assert so.culgt_mag_fix_gauge(ctypes.c_void_p(16), ctypes.byref(q._c()), None, None, None) == lib.ERR_ARG
+    bad = lib.Params.defaults(3, (4, 4, 4, 4), gauge=lib.MAG)
+    bad.omega = 2.5
+    assert so.culgt_mag_fix_gauge(ctypes.c_void_p(16), ctypes.byref(bad._c()), None, None,
+                                  ctypes.c_void_p(16)) != lib.OK
 
 
 def test_coulomb_anneal_rejects_before_device_work(lib):

@@ -119,6 +119,32 @@ def test_mag_fix_fp64_matches_oracle(cu, orc, nc):
     assert np.abs(np.abs(from_dev(d, U.shape)) - np.abs(ref)).max() < 1e-9
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_df"])
+@pytest.mark.parametrize("nc", [2, 3])
+def test_mag_fix_returns_the_gauge_transformation(cu, orc, nc, precision):
+    """culgt_mag_fix_gauge: the output links are the input transformed by the
+    returned g (to the accuracy of its accumulation), g is unitary, and the
+    fix converges like the FP64 oracle's MAG fix (its sweep count in FP64,
+    F_MAG within 1e-10)."""
+    prec = {"fp64": cu.FP64, "mixed": cu.MIXED, "mixed_df": cu.MIXED_DF}[precision]
+    dims = (4, 4, 4, 4)
+    V = int(np.prod(dims))
+    U = synth.gauge_config(dims, nc, 0.3, 1)
+    d = to_dev(U)
+    gauge = torch.zeros(V * nc * nc * 2, dtype=torch.float64, device="cuda")
+    p = cu.Params.defaults(nc, dims, precision=prec, check_every=5, reunit_every=50, max_sweeps=5000)
+    r = cu.culgt_mag_fix_gauge(d, p, gauge)
+    rr = orc.mag_fix(U.copy(), dims, nc, 1.7, 1e-12, 5000, 5, 50)
+    assert r.status == cu.OK and r.theta < 1e-12
+    if prec == cu.FP64:
+        assert r.sweeps_fp64 == rr["sweeps"]
+    assert r.F == pytest.approx(rr["F"], rel=1e-10)
+    g = gauge.cpu().numpy().view(np.complex128).reshape(V, nc, nc)
+    assert np.abs(g @ np.swapaxes(g.conj(), 1, 2) - np.eye(nc)).max() < 1e-13
+    tol = 1e-12 if prec == cu.FP64 else 1e-10
+    assert np.abs(from_dev(d, U.shape) - synth.gauge_transform(U, dims, g)).max() < tol
+
+
 @pytest.mark.parametrize("precision", ["mixed", "mixed_df", "df"])
 @pytest.mark.parametrize("nc", [2, 3])
 def test_mag_fix_reduced_and_mixed(cu, orc, nc, precision):
